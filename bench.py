@@ -1,0 +1,312 @@
+"""Benchmark of the dOpInf hot path on GB300: one step = Steps II-IV on one snapshot matrix.
+
+Workload (2D step-flow shape): n = 3 variables x 400,000 rows = 1.2M, k = 600 snapshots,
+FP64, seeded r_true = 40 quadratic system lifted with per-variable scales 1e-2, 1e1, 1e3;
+Step IV fits r in {10, 20, 30} over the 8 x 8 grid logspace(-10, 0, 8) x logspace(-4, 4, 8)
+with 5000-step RK4 rollouts (continuous mode, snapshot spacing 0.01).
+
+Contract: prints ONE JSON line (rank 0).  value = whole-job pipelines per second (inputs
+resident in HBM), e2e = the same through the C ABI with the snapshot matrix copied from
+pinned host memory every step and the results copied back.  --impl reference times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import dataclasses
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gram TFLOP/s + dOpInf learn time, split-prec/batched vs FP64 plain, at stated err"
+UNIT = "dOpInf pipelines/s"
+WORKLOAD = "stepflow"
+FP64_NOMINAL_TF, BF16_NOMINAL_TF = 1.25, 2250.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--stage", default="all", choices=["all", "gram"],
+                   help="gram: time only the Gram of the transformed matrix (for profiling)")
+    p.add_argument("--n-per-var", type=int, default=0, help="override rows per variable (smaller case)")
+    return p.parse_args()
+
+
+def workload(name):
+    from paper_2504_14338_gb300 import synth
+    return synth.WORKLOADS[name]
+
+
+def config_of(w):
+    return {"workload": "%s: n=%dx%d=%d, k=%d, r_true=%d, r=%s, %dx%d grid, %d-step %s, %s" % (
+        w.name, w.n_vars, w.n_per_var, w.n, w.k, w.r_true, list(w.r_list), w.n_beta1, w.n_beta2, w.n_steps,
+        "RK4" if w.mode == "continuous" else "discrete", w.dtype),
+        "n": w.n, "k": w.k, "r_list": list(w.r_list), "grid": [w.n_beta1, w.n_beta2], "n_steps": w.n_steps,
+        "gram_mode": "fp64", "l2": "inputs larger than L2 (%.2f GB snapshot matrix)" % (w.n * w.k * 8 / 1e9)}
+
+
+# ------------------------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self):
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"),
+                                          "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ oracle
+def oracle_sample(w):
+    """Times the FP64 CPU oracle on a bounded sample; returns (seconds per full pipeline, desc)."""
+    from oracle import dopinf_oracle as O
+    from paper_2504_14338_gb300 import synth
+    frac = 16
+    ws = dataclasses.replace(w, name=w.name + "-sample", n_per_var=w.n_per_var // frac)
+    Qn, _ = synth.snapshots_numpy(ws)
+    t0 = time.perf_counter()
+    Qt, _, _, _ = O.transform(Qn, ws.var_row_offsets())
+    t1 = time.perf_counter()
+    D = O.gram(Qt)
+    t2 = time.perf_counter()
+    r_max = max(w.r_list)
+    red = O.reduce(D, r_fixed=r_max)
+    t3 = time.perf_counter()
+    b1, b2 = w.beta1s(), w.beta2s()
+    t_learn = 0.0
+    for r in w.r_list:  # two candidates per r from the middle of the grid
+        s = time.perf_counter()
+        O.learn(red["Qhat"], [r], [b1[len(b1) // 2]], b2[len(b2) // 2 - 1:len(b2) // 2 + 1], w.n_steps,
+                mode=w.mode, dt=w.snap_dt)
+        t_learn += (time.perf_counter() - s) * len(b1) * len(b2) / 2
+    per_pipeline = frac * ((t1 - t0) + (t2 - t1)) + (t3 - t2) + t_learn
+    desc = ("Steps II-III on 1/%d of the rows (n=%d, k=%d), scaled x%d; full reduce; Step IV on two (beta1, "
+            "beta2) per r (%d-step %s rollouts), scaled x%d; oracle as committed (numpy FP64)" % (
+                frac, ws.n, w.k, frac, w.n_steps, w.mode, len(b1) * len(b2) // 2))
+    return per_pipeline, desc, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    times = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        per, desc, _ = oracle_sample(w)
+        if i >= args.warmup:
+            times.append(per)
+    sec = float(np.mean(times))
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / sec, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
+            "cpu_baseline": {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": 1.0 / sec, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2504_14338_gb300 import dopinf as dp
+    from paper_2504_14338_gb300 import synth
+
+    w0 = workload(args.workload)
+    w = dataclasses.replace(w0, seed=w0.seed + 7919 * rank)
+    if args.n_per_var:
+        w = dataclasses.replace(w, n_per_var=args.n_per_var)
+    dev = torch.device("cuda", local)
+    QT = synth.snapshots_torch(w, dev)          # (k, n) row-major = column-major n x k
+    Q = QT.t()
+    offs = w.var_row_offsets()
+    b1, b2 = w.beta1s(), w.beta2s()
+    r_max = max(w.r_list)
+    mode = dp.CONTINUOUS_RK4 if w.mode == "continuous" else dp.DISCRETE
+    stream = torch.cuda.current_stream()
+    ws = dp.Workspace(dev)
+
+    ev = {}
+    if args.stage == "gram":
+        dp.dopinf_transform(Q, offs, ws=ws)
+        D = torch.zeros(w.k, w.k, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            dp.dopinf_gram(Q, D=D, ws=ws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            dp.dopinf_gram(Q, D=D, ws=ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        if rank == 0:
+            print(json.dumps({"stage": "gram", "n": w.n, "k": w.k, "ms": ms,
+                              "tflops": w.n * w.k * (w.k + 1) / ms / 1e9}), flush=True)
+        return
+
+    def step(record=False):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(stream)
+        dp.dopinf_transform(Q, offs, ws=ws)
+        e[1].record(stream)
+        D = dp.dopinf_gram(Q, ws=ws)
+        e[2].record(stream)
+        red = dp.dopinf_reduce(D, r_cap=r_max, r_fixed=r_max, ws=ws)
+        e[3].record(stream)
+        res = dp.dopinf_learn(red["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode, dt=w.snap_dt, ws=ws)
+        e[4].record(stream)
+        if record:
+            ev.setdefault("stages", []).append(e)
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        res = step(record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    names = ["transform", "gram", "reduce", "learn"]
+    stage = {nm: float(np.mean([es[i].elapsed_time(es[i + 1]) for es in ev["stages"]])) for i, nm in enumerate(names)}
+    gram_flops = w.n * w.k * (w.k + 1)
+    gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
+
+    # e2e: host snapshot matrix (pinned) -> device, the pipeline through the C ABI, results back
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(QT.shape, dtype=QT.dtype, pin_memory=True)
+        host.copy_(QT)
+        n_e2e = max(1, min(args.steps, 2))
+        h2d = host.numel() * host.element_size()
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        d2h = 0
+        for _ in range(n_e2e):
+            QT.copy_(host, non_blocking=True)
+            res2 = step()
+            out = [res2["train_err"], res2["status"], res2["O_best"]]
+            outs = [o.cpu() for o in out]
+            d2h = sum(o.numel() * o.element_size() for o in outs)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - s0) / n_e2e
+        e2e_val = world / e2e_s
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    fp64_peak = bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+    roof = {"kernel": "tn_partial (FP64 Gram, split-K) + tn_reduce", "bound": "alu", "achieved": gram_tf * 1e3,
+            "peak": fp64_peak * 1e3, "unit": "GFLOP/s", "frac": gram_tf / fp64_peak,
+            "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)",
+            "traffic": None, "algorithmic_flops_per_launch": gram_flops}
+    k = w.k
+    launches = 3 + 2 + (3 * (k - 2) + 8) + (8 * len(w.r_list) + 1)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        per, desc, wall = oracle_sample(w)
+        cpu = {"value": 1.0 / per, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "sample_wall_s": wall}
+    if rank == 0:
+        best = res["best"]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
+                "stages_ms": stage, "gram_tflops_fp64": gram_tf, "learn_s": stage["learn"] / 1e3,
+                "best": {"index": best, "r": res.get("r"), "beta1": res.get("beta1"), "beta2": res.get("beta2")},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "clocks": ck}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

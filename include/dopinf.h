@@ -1,0 +1,180 @@
+/*
+ * dopinf.h - C ABI of the GB300 (sm_103a) dOpInf hot path.
+ *
+ * Distributed Operator Inference (Farcas, Gundevia, Munipalli, Willcox, arXiv 2504.14338)
+ * on one GPU: Step II (centering and max-abs scaling, Section 3.3), Step III (method of
+ * snapshots Gram, eigensolve, retained energy and basis-free projection, Section 3.4,
+ * eqs. mos_partitioned, mos_Sigma_W, ret_energy, MoS_POD_basis, dOpInf_projection) and
+ * Step IV (quadratic OpInf with a regularisation grid search and ROM rollouts, Section 3.5,
+ * eqs. ROM_quad_time_cont, ROM_quad_time_discrete, OpInf_reg,
+ * OpInf_data_matrices_discrete).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are caller-owned DEVICE memory unless the comment says "host".  The library
+ *    never frees caller memory and allocates no device memory: scratch comes from the
+ *    caller's workspace (ws, ws_bytes), sized by the matching *_workspace() query.  The
+ *    workspace must be 256-byte aligned.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless the comment says the call synchronises it.
+ *  - Matrices are column-major with an explicit leading dimension.  The snapshot matrix
+ *    Q is n x k: column t (snapshot t) holds rows 0..n-1 contiguously, rows are stacked
+ *    variable by variable (all rows of variable 0, then variable 1, ...).
+ *  - Argument errors return DOPINF_E_ARG before anything is launched.  Conditions the
+ *    GPU detects (non-finite data, a zero scale) are OR-ed as DOPINF_FLAG_* bits into the
+ *    optional device word dev_flags; calls that synchronise also return them as codes.
+ *  - Thread safety: calls on different streams with disjoint workspaces are independent.
+ */
+#ifndef DOPINF_H
+#define DOPINF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum dopinf_status {
+  DOPINF_OK = 0,
+  DOPINF_E_ARG = -1,          /* invalid argument (null pointer, bad size, small workspace) */
+  DOPINF_E_CUDA = -2,         /* a CUDA runtime call failed */
+  DOPINF_E_NONFINITE = -4,    /* NaN or Inf found in the data */
+  DOPINF_E_RANK = -6,         /* lambda_r <= 0, or the energy target is not reached by r_cap */
+  DOPINF_E_NO_STABLE = -7,    /* no (r, beta1, beta2) candidate is finite and bounded */
+  DOPINF_E_UNSUPPORTED = -9   /* valid request this build does not implement */
+};
+
+/* bits OR-ed into a device flag word */
+#define DOPINF_FLAG_NONFINITE 1u   /* NaN/Inf in the data */
+#define DOPINF_FLAG_ZERO_SCALE 2u  /* a variable block is constant after centering; scale := 1 */
+
+enum dopinf_dtype { DOPINF_F64 = 0, DOPINF_F32 = 1 };
+
+#define DOPINF_CENTER 1u
+#define DOPINF_SCALE 2u
+
+enum dopinf_gram_mode {
+  DOPINF_GRAM_FP64 = 0,      /* FP64 FMA over every row (the plain path) */
+  DOPINF_GRAM_BF16X3 = 1     /* split precision on the tensor cores (see dopinf_gram) */
+};
+
+enum dopinf_rom_mode {
+  DOPINF_DISCRETE = 0,       /* q[t+1] = A q[t] + H (q[t] x q[t])_u + c  (eq. ROM_quad_time_discrete) */
+  DOPINF_CONTINUOUS_RK4 = 1  /* q' = A q + H (q x q)_u + c, central-difference derivatives, RK4 rollout */
+};
+
+/* Human-readable name of a status code (static storage). */
+const char* dopinf_status_string(int status);
+
+/* ------------------------------------------------------------------------------------
+ * Step II (Section 3.3): centre each row by its temporal mean, then divide each variable
+ * block by the largest |centred value| of the block.
+ *
+ * Q            in/out, n x k, element type dtype, leading dimension ldq >= n (elements).
+ * n_vars       number of variable blocks (1..1024).
+ * var_row_offsets host, n_vars + 1 nondecreasing row offsets, [0] = 0, [n_vars] = n.
+ * flags        DOPINF_CENTER | DOPINF_SCALE.
+ * row_mean     out, n doubles: mean_i = (sum_t Q[i,t], summed in t order in FP64) / k.
+ * var_scale    out, n_vars doubles: max_{i in var, t} |Q[i,t] - mean_i|, rounded as the
+ *              centred values are (FP64 data: FP64; FP32 data: fp32(fp64(x) - mean));
+ *              a zero scale is replaced by 1 and DOPINF_FLAG_ZERO_SCALE is set.
+ * Results:     FP64: Q = (Q - mean) / scale, each operation rounded to nearest.
+ *              FP32: Q = fp32(fp64(Q) - mean) / fp32(scale), the division in FP32.
+ *              Bit-identical to the definition (no reassociation, no contraction).
+ * dev_flags    optional device unsigned int; DOPINF_FLAG_* bits are OR-ed in.
+ * Workspace:   dopinf_transform_workspace(n, n_vars) bytes.
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_transform_workspace(int64_t n, int n_vars);
+int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int n_vars,
+                     const int64_t* var_row_offsets, unsigned flags, double* row_mean,
+                     double* var_scale, unsigned* dev_flags, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Step III Gram matrix (eq. mos_partitioned): D = Q^T Q, k x k FP64, column-major,
+ * leading dimension ldd >= k, both triangles written.  accumulate = 1 adds Q^T Q to D
+ * (row blocks of one snapshot matrix, the paper's partitioned sum).
+ *
+ * DOPINF_GRAM_FP64: Q is FP64 or FP32 (promoted exactly); FP64 products and sums over row
+ *   chunks; the chunk partials are added in a fixed order, so the result is run-to-run
+ *   bit-reproducible.
+ * Workspace: dopinf_gram_workspace(n, k, dtype, mode) bytes.
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode);
+int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
+                int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Step III eigensolve and projection (eqs. mos_Sigma_W, ret_energy, MoS_POD_basis,
+ * dOpInf_projection).  Symmetric eigendecomposition of D (k x k FP64, ldd), leading
+ * r_cap eigenpairs in descending order; sign of each eigenvector: its largest-magnitude
+ * entry is positive.  The energy denominator is trace(D).
+ *
+ * r_fixed > 0: r = r_fixed; otherwise r = the smallest r with
+ *   sum_{i<=r} lambda_i / trace(D) > energy_target (strict), which must be <= r_cap.
+ * r_cap        number of eigenpairs computed and of rows of Qhat (1 <= r_cap <= k).
+ * eigvals      out, r_cap doubles, descending.
+ * Tr           out, k x r_cap (ld k): T = U Lambda^{-1/2} (columns for lambda_i > 0).
+ * Qhat         out, r_cap x k (ld r_cap): Qhat = T^T D; column t is the reduced snapshot t.
+ *              The Qhat of any r <= r_cap is its leading r rows.
+ * r_out, trace_out  host, the chosen r and trace(D).
+ * Synchronises the stream (r is returned on the host).  Returns DOPINF_E_RANK if
+ * lambda_r <= 0 or the energy target is not reached within r_cap.
+ * Workspace: dopinf_reduce_workspace(k, r_cap) bytes.
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_reduce_workspace(int64_t k, int r_cap);
+int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed,
+                  int r_cap, int* r_out, double* trace_out, double* eigvals, double* Tr,
+                  double* Qhat, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Step IV: quadratic OpInf with the (r, beta1, beta2) grid search (eqs. OpInf_reg,
+ * OpInf_data_matrices_discrete; the training error and growth criterion of Step IV).
+ *
+ * Qhat       r_max x k reduced data (ld ldqh >= r_max), column t = snapshot t.
+ * r_list     host, n_r reduced dimensions (1 <= r <= r_max, k-1 (discrete) or k-2
+ *            (continuous) rows of data are used).
+ * beta1, beta2  host, n_b1 and n_b2 regularisation values.
+ * Candidates are numbered r-major, then beta1, then beta2:
+ *   c = (ir * n_b1 + i1) * n_b2 + i2.
+ * For each candidate: data matrix Dhat = [q, (q_i q_j)_{i<=j}, 1] over the training rows,
+ * G = Dhat^T Dhat, B = Dhat^T Y, Cholesky solve of (G + diag(beta1 1_r, beta2 1_s,
+ * beta1)) O^T = B; rollout of n_steps states (initial state included) from Qhat[:, 0];
+ * train_err = max_{t<k} ||q~_t - qhat_t|| / ||qhat_t||; growth = max_{t,i} |q~ - mu| /
+ * max_{t<k,i} |qhat - mu| (mu = temporal mean of Qhat).  Valid iff the factorisation
+ * succeeded, the rollout is finite and growth < max_growth.  A rollout stops early once
+ * the candidate is certainly invalid (growth already >= max_growth or non-finite).
+ *
+ * mode, dt   DOPINF_DISCRETE, or DOPINF_CONTINUOUS_RK4 with snapshot spacing dt.
+ * train_err, growth  out (device), n_cand doubles (+Inf for invalid candidates).
+ * cand_status out (device), n_cand ints: 0 valid, 1 Cholesky breakdown, 2 non-finite,
+ *            3 growth >= max_growth.
+ * best_out   host: best candidate index, -1 if none is valid.
+ * O_best     out (device), r_max x (d_max) doubles, ld r_max: operators [A | H | c] of
+ *            the best candidate (its r x d leading block), d = r + r(r+1)/2 + 1.
+ * Synchronises the stream.  Returns DOPINF_E_NO_STABLE if no candidate is valid.
+ * Workspace: dopinf_learn_workspace(...) bytes.
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1,
+                              int n_b2);
+int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list,
+                 int n_r, const double* beta1, int n_b1, const double* beta2, int n_b2,
+                 int mode, double dt, int64_t n_steps, double max_growth, double* train_err,
+                 double* growth, int* cand_status, int* best_out, double* O_best, void* ws,
+                 size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Rollout of one quadratic ROM (eq. ROM_quad_time_discrete, or RK4 on
+ * eq. ROM_quad_time_cont): O is r x d (ld ldo >= r), d = r + r(r+1)/2 + 1, columns
+ * [A | H | c] with H's columns ordered (i, j), i <= j, i-major.  q0 has r entries.
+ * Qtilde out, n_steps x r row-major (row t = state t, row 0 = q0).  finite out (device
+ * int): 1 if every state is finite.  No workspace.
+ * ------------------------------------------------------------------------------------ */
+int dopinf_rollout(const double* O, int r, int64_t ldo, const double* q0, int64_t n_steps,
+                   int mode, double dt, double* Qtilde, int* finite, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOPINF_H */

@@ -1,0 +1,90 @@
+// Internal helpers of the dOpInf CUDA library (sm_103a).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "../../include/dopinf.h"
+
+#define DOPINF_API extern "C" __attribute__((visibility("default")))
+
+namespace dopinf {
+
+constexpr int kMaxVars = 64;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+// Carves aligned sub-buffers out of a caller workspace.  With base == nullptr it only
+// counts bytes, so the *_workspace() queries and the entry points share one layout.
+struct Carver {
+  char* base;
+  size_t used = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    size_t off = used;
+    used = align_up(used + count * sizeof(T));
+    return base ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+};
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? DOPINF_OK : DOPINF_E_CUDA; }
+
+// Launch-error check after a kernel launch (does not synchronise).
+inline int launch_status() { return cuda_status(cudaGetLastError()); }
+
+inline bool misaligned(const void* p, size_t a = kAlign) {
+  return (reinterpret_cast<uintptr_t>(p) % a) != 0;
+}
+
+#define DOPINF_TRY(expr)                 \
+  do {                                   \
+    int _st = (expr);                    \
+    if (_st != DOPINF_OK) return _st;    \
+  } while (0)
+
+#define DOPINF_CUDA(expr) DOPINF_TRY(::dopinf::cuda_status(expr))
+
+// ---------------------------------------------------------------------------------------
+// Generic FP64 "TN" product C = A^T B (A: K x M, B: K x N, both column-major, element type
+// double or float promoted exactly), split over K with a fixed-order reduction.  Used by the
+// Gram of Step III and the normal equations of Step IV.  Implemented in gram_fp64.cu.
+// sym = 1 requires A == B, M == N and computes only the upper tiles, mirroring them.
+// ---------------------------------------------------------------------------------------
+size_t tn_workspace(int64_t K, int64_t M, int64_t N, int sym);
+int tn_product(const void* A, int64_t lda, const void* B, int64_t ldb, int dtype, int64_t K,
+               int64_t M, int64_t N, int sym, int accumulate, double* C, int64_t ldc, void* ws,
+               size_t ws_bytes, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
+// Batched ROM rollouts (rollout.cu): one CTA per candidate.
+// ---------------------------------------------------------------------------------------
+struct RolloutArgs {
+  const double* O;      // candidate c's operator at O + c * o_stride, column-major r x d, ld ldo
+  int64_t o_stride, ldo;
+  int r, d;
+  int mode;
+  double dt;
+  int64_t n_steps;
+  const double* q0;     // initial state (r), for metrics runs: Qhat column 0
+  // metrics (optional)
+  const double* Qhat;   // reference data r_max x k (ld ldqh) for the training error
+  int64_t ldqh, k;
+  const double* mu;     // temporal mean of the reference (r)
+  const double* denom;  // max_{t<k,i} |qhat - mu|
+  double max_growth;
+  double* train_err;    // per candidate (indexed by cand0 + blockIdx.x)
+  double* growth;
+  int* status;
+  int cand0;
+  // trajectory output (optional): n_steps x r row-major; rows after the first non-finite
+  // state are not written
+  double* traj;
+  int* finite;
+};
+
+int launch_rollouts(const RolloutArgs& a, int n_cand, bool metrics, bool traj, cudaStream_t st);
+
+}  // namespace dopinf

@@ -1,0 +1,461 @@
+// Step III of dOpInf (Section 3.4): symmetric eigendecomposition of the Gram matrix
+// (eq. mos_Sigma_W), the retained-energy rank (eq. ret_energy) and the basis-free
+// projection T_r = U_r Lambda_r^{-1/2}, Qhat = T_r^T D (eqs. MoS_POD_basis, dOpInf_projection).
+//
+// Only the leading r_cap eigenpairs are formed (the paper notes that a partial eigensolve
+// suffices when r is known; the energy rule needs only trace(D) besides them):
+//  1. Householder reduction of D to tridiagonal form T = H^T D H, one reflector per column,
+//     three launches per column: reflector, symmetric matrix-vector product, rank-2 update.
+//  2. the r_cap largest eigenvalues of T by Sturm-count multisection, one warp per
+//     eigenvalue, 32 trial points per round;
+//  3. their eigenvectors by inverse iteration with the partially pivoted tridiagonal LU,
+//     re-orthogonalised (modified Gram-Schmidt, twice) against earlier vectors whose
+//     eigenvalues lie within 1e-3 ||T||;
+//  4. back-transformation by the stored reflectors, sign rule (largest-magnitude entry
+//     positive, lowest index on ties);
+//  5. T_r and Qhat = T_r^T D with the FP64 TN product.
+// All arithmetic is FP64; every reduction has a fixed order.
+#include "common.cuh"
+#include <math.h>
+#include <float.h>
+
+namespace dopinf {
+namespace {
+
+constexpr int EB = 256;  // threads per block for the reduction kernels
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  // fixed-order tree: warp shuffles, then the warp partials in warp order
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) s += sh[i];
+  return s;
+}
+
+// Reflector of column j: x = A[j+1:k, j] -> (I - tau v v^T) x = beta e1 with v[0] = 1.
+// v overwrites A[j+1:k, j]; d[j] = A[j][j], e[j] = beta.
+__global__ void __launch_bounds__(EB) hh_gen(double* A, int64_t k, int64_t j, double* d, double* e, double* tau) {
+  __shared__ double sh[32];
+  double* x = A + j * k;  // column j
+  double part = 0.0;
+  for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) part += x[i] * x[i];
+  const double sigma2 = block_sum(part, sh);
+  const double x0 = x[j + 1];
+  double t, beta, scal;
+  if (sigma2 == 0.0) {
+    t = 0.0;
+    beta = x0;
+    scal = 0.0;
+  } else {
+    const double nrm = sqrt(x0 * x0 + sigma2);
+    beta = x0 >= 0.0 ? -nrm : nrm;
+    t = (beta - x0) / beta;
+    scal = 1.0 / (x0 - beta);
+  }
+  __syncthreads();
+  if (t != 0.0)
+    for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) x[i] *= scal;
+  if (threadIdx.x == 0) {
+    d[j] = x[j];
+    e[j] = beta;
+    tau[j] = t;
+    x[j + 1] = 1.0;
+  }
+}
+
+// p = tau * A22 v with A22 = A[j+1:, j+1:], one warp per row (row i of A22 = column i).
+__global__ void __launch_bounds__(EB) hh_symv(const double* A, int64_t k, int64_t j, const double* tau, double* p) {
+  const double t = tau[j];
+  if (t == 0.0) return;
+  const int64_t m = k - j - 1;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const double* col = A + (j + 1 + row) * k + (j + 1);
+  const double* v = A + j * k + (j + 1);
+  double s = 0.0;
+  for (int64_t l = lane; l < m; l += 32) s = fma(col[l], v[l], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) p[row] = t * s;
+}
+
+// A22 -= v w^T + w v^T with w = p - (tau/2)(p.v) v.  Each block recomputes p.v in a fixed
+// order and updates a group of columns of A22 (full symmetric storage).
+constexpr int R2_COLS = 16;
+__global__ void __launch_bounds__(EB) hh_rank2(double* A, int64_t k, int64_t j, const double* tau, const double* p) {
+  __shared__ double sh[32];
+  const double t = tau[j];
+  if (t == 0.0) return;
+  const int64_t m = k - j - 1;
+  const double* v = A + j * k + (j + 1);
+  double part = 0.0;
+  for (int64_t l = threadIdx.x; l < m; l += blockDim.x) part = fma(p[l], v[l], part);
+  const double alpha = -0.5 * t * block_sum(part, sh);
+  const int64_t c0 = (int64_t)blockIdx.x * R2_COLS;
+  for (int cc = 0; cc < R2_COLS; ++cc) {
+    const int64_t c = c0 + cc;
+    if (c >= m) break;
+    const double vc = v[c], wc = fma(alpha, vc, p[c]);
+    double* col = A + (j + 1 + c) * k + (j + 1);
+    for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+      const double wr = fma(alpha, v[r], p[r]);
+      col[r] = col[r] - v[r] * wc - wr * vc;
+    }
+  }
+}
+
+__global__ void hh_tail(const double* A, int64_t k, double* d, double* e, double* tau) {
+  if (threadIdx.x != 0) return;
+  if (k >= 2) {
+    d[k - 2] = A[(k - 2) * k + (k - 2)];
+    e[k - 2] = A[(k - 2) * k + (k - 1)];
+    tau[k - 2] = 0.0;
+  }
+  d[k - 1] = A[(k - 1) * k + (k - 1)];
+  e[k - 1] = 0.0;
+  tau[k - 1] = 0.0;
+}
+
+// Gershgorin interval and the pivot floor of the Sturm count.
+__device__ void tri_bounds(const double* d, const double* e, int64_t k, double& lo, double& hi, double& pivmin) {
+  lo = DBL_MAX;
+  hi = -DBL_MAX;
+  double emax2 = 0.0;
+  for (int64_t i = 0; i < k; ++i) {
+    const double el = i > 0 ? fabs(e[i - 1]) : 0.0, er = i + 1 < k ? fabs(e[i]) : 0.0;
+    lo = fmin(lo, d[i] - el - er);
+    hi = fmax(hi, d[i] + el + er);
+    if (i + 1 < k) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  pivmin = DBL_MIN * fmax(1.0, emax2);
+  const double w = fmax(fabs(lo), fabs(hi));
+  lo -= 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
+  hi += 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
+}
+
+// Number of eigenvalues of T smaller than x (Sturm sequence of the LDL^T pivots).
+__device__ int64_t sturm_count(const double* d, const double* e, int64_t k, double x, double pivmin) {
+  int64_t cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int64_t i = 1; i < k; ++i) {
+    q = d[i] - x - (e[i - 1] * e[i - 1]) / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// One warp per wanted eigenvalue (index idx in descending order = ascending index k-1-idx).
+// Each round evaluates 32 interior points of [lo, hi] and keeps the sub-interval that holds
+// the eigenvalue: a 33-fold reduction per round.
+__global__ void tri_multisect(const double* d, const double* e, int64_t k, int r_cap, double* lam, double* tnorm) {
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (idx >= r_cap) return;
+  double lo, hi, pivmin;
+  tri_bounds(d, e, k, lo, hi, pivmin);
+  const double tn = fmax(fabs(lo), fabs(hi));
+  if (idx == 0 && lane == 0) *tnorm = tn;
+  const int64_t a = k - 1 - idx;  // ascending index
+  for (int round = 0; round < 64; ++round) {
+    const double width = hi - lo;
+    if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_EPSILON * tn + 4.0 * pivmin) break;
+    const double x = lo + width * (double)(lane + 1) / 33.0;
+    const int64_t c = sturm_count(d, e, k, x, pivmin);
+    // the eigenvalue lies below x iff count(x) > a
+    const unsigned above = __ballot_sync(0xffffffffu, c > a);
+    const int first = above ? __ffs(above) - 1 : 32;  // first trial point above the eigenvalue
+    const double nlo = first == 0 ? lo : __shfl_sync(0xffffffffu, x, first - 1 < 0 ? 0 : first - 1);
+    const double nhi = first == 32 ? hi : __shfl_sync(0xffffffffu, x, first > 31 ? 31 : first);
+    if (nlo == lo && nhi == hi) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) lam[idx] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double start_value(int64_t i, int j) {
+  // deterministic pseudo-random start vector in (-1, 1): a 64-bit integer hash of (i, j)
+  unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull ^ ((unsigned long long)j << 32 | 0x5bd1e995u);
+  h ^= h >> 31;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 29;
+  return ((double)(h >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// Inverse iteration, one thread per eigenvector; per-thread scratch is interleaved
+// (element i of vector j at [i * r_cap + j]) so that the threads' accesses coalesce.
+__global__ void tri_invit(const double* d, const double* e, int64_t k, int r_cap, const double* lam,
+                          const double* tnorm, double* Dg, double* Du, double* Du2, double* Dl,
+                          unsigned char* piv, double* Z) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= r_cap) return;
+  const double lj = lam[j];
+  const double eps_piv = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
+#define AT(arr, i) arr[(size_t)(i) * r_cap + j]
+  for (int64_t i = 0; i < k; ++i) {
+    AT(Dg, i) = d[i] - lj;
+    if (i + 1 < k) {
+      AT(Du, i) = e[i];
+      AT(Dl, i) = e[i];
+    }
+  }
+  // T - lambda I = P L U, partial pivoting by rows
+  for (int64_t i = 0; i + 1 < k; ++i) {
+    const double di = AT(Dg, i), li = AT(Dl, i);
+    if (fabs(di) >= fabs(li)) {
+      AT(piv, i) = 0;
+      const double f = di != 0.0 ? li / di : 0.0;
+      AT(Dl, i) = f;
+      AT(Dg, i + 1) = AT(Dg, i + 1) - f * AT(Du, i);
+      if (i + 2 < k) AT(Du2, i) = 0.0;
+    } else {
+      AT(piv, i) = 1;
+      const double f = di / li;
+      AT(Dg, i) = li;
+      AT(Dl, i) = f;
+      const double tmp = AT(Du, i);
+      const double dn = AT(Dg, i + 1);
+      AT(Du, i) = dn;
+      AT(Dg, i + 1) = tmp - f * dn;
+      if (i + 2 < k) {
+        const double un = AT(Du, i + 1);
+        AT(Du2, i) = un;
+        AT(Du, i + 1) = -f * un;
+      }
+    }
+  }
+  for (int64_t i = 0; i < k; ++i)
+    if (fabs(AT(Dg, i)) < eps_piv) AT(Dg, i) = AT(Dg, i) < 0.0 ? -eps_piv : eps_piv;
+  for (int64_t i = 0; i < k; ++i) AT(Z, i) = start_value(i, j);
+  for (int it = 0; it < 3; ++it) {
+    // forward: L^{-1} P b
+    for (int64_t i = 0; i + 1 < k; ++i) {
+      const double f = AT(Dl, i);
+      if (AT(piv, i)) {
+        const double bi = AT(Z, i), bn = AT(Z, i + 1);
+        AT(Z, i) = bn;
+        AT(Z, i + 1) = bi - f * bn;
+      } else {
+        AT(Z, i + 1) = AT(Z, i + 1) - f * AT(Z, i);
+      }
+    }
+    // backward: U^{-1}
+    double nrm2 = 0.0;
+    for (int64_t i = k - 1; i >= 0; --i) {
+      double s = AT(Z, i);
+      if (i + 1 < k) s -= AT(Du, i) * AT(Z, i + 1);
+      if (i + 2 < k) s -= AT(Du2, i) * AT(Z, i + 2);
+      s /= AT(Dg, i);
+      AT(Z, i) = s;
+    }
+    double mx = 0.0;
+    for (int64_t i = 0; i < k; ++i) mx = fmax(mx, fabs(AT(Z, i)));
+    const double inv_mx = 1.0 / mx;
+    for (int64_t i = 0; i < k; ++i) {
+      const double z = AT(Z, i) * inv_mx;
+      nrm2 += z * z;
+      AT(Z, i) = z;
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int64_t i = 0; i < k; ++i) AT(Z, i) *= inv;
+  }
+#undef AT
+}
+
+// Modified Gram-Schmidt (twice) of each vector against the earlier vectors of its cluster
+// (|lambda_i - lambda_j| <= 1e-3 ||T||), then normalisation.  One block, vectors in order.
+__global__ void __launch_bounds__(EB) tri_orth(int64_t k, int r_cap, const double* lam, const double* tnorm, double* Z) {
+  __shared__ double sh[32];
+  const double tol = 1e-3 * (*tnorm);
+#define ZZ(i, j) Z[(size_t)(i) * r_cap + (j)]
+  for (int j = 1; j < r_cap; ++j) {
+    int first = j;
+    while (first > 0 && fabs(lam[first - 1] - lam[j]) <= tol) --first;
+    if (first == j) continue;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = first; i < j; ++i) {
+        double part = 0.0;
+        for (int64_t r = threadIdx.x; r < k; r += blockDim.x) part = fma(ZZ(r, i), ZZ(r, j), part);
+        const double dot = block_sum(part, sh);
+        for (int64_t r = threadIdx.x; r < k; r += blockDim.x) ZZ(r, j) = ZZ(r, j) - dot * ZZ(r, i);
+        __syncthreads();
+      }
+    }
+    double part = 0.0;
+    for (int64_t r = threadIdx.x; r < k; r += blockDim.x) part = fma(ZZ(r, j), ZZ(r, j), part);
+    const double inv = 1.0 / sqrt(block_sum(part, sh));
+    for (int64_t r = threadIdx.x; r < k; r += blockDim.x) ZZ(r, j) *= inv;
+    __syncthreads();
+  }
+#undef ZZ
+}
+
+// U[:, j] = H_0 H_1 ... H_{k-3} z_j, then the sign rule and T_r = U_r Lambda^{-1/2}.
+// One block per eigenvector; the vector lives in shared memory.
+__global__ void __launch_bounds__(EB) hh_back(const double* A, int64_t k, int r_cap, const double* tau,
+                                              const double* lam, const double* Z, double* U, double* Tr) {
+  extern __shared__ double z[];
+  __shared__ double sh[32];
+  __shared__ int s_arg;
+  const int j = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) z[i] = Z[(size_t)i * r_cap + j];
+  __syncthreads();
+  for (int64_t jj = k - 3; jj >= 0; --jj) {
+    const double t = tau[jj];
+    if (t == 0.0) continue;
+    const double* v = A + jj * k;  // v at rows jj+1..k-1, v[jj+1] = 1
+    double part = 0.0;
+    for (int64_t i = jj + 1 + threadIdx.x; i < k; i += blockDim.x) part = fma(v[i], z[i], part);
+    const double s = t * block_sum(part, sh);
+    for (int64_t i = jj + 1 + threadIdx.x; i < k; i += blockDim.x) z[i] = fma(-s, v[i], z[i]);
+    __syncthreads();
+  }
+  // sign rule: the entry of largest magnitude is positive (lowest index on ties)
+  if (threadIdx.x == 0) {
+    double best = -1.0;
+    int arg = 0;
+    for (int64_t i = 0; i < k; ++i) {
+      const double a = fabs(z[i]);
+      if (a > best) {
+        best = a;
+        arg = (int)i;
+      }
+    }
+    s_arg = arg;
+  }
+  __syncthreads();
+  const double sgn = z[s_arg] < 0.0 ? -1.0 : 1.0;
+  const double l = lam[j];
+  const double sc = l > 0.0 ? 1.0 / sqrt(l) : 0.0;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
+    const double u = sgn * z[i];
+    U[i + (size_t)j * k] = u;
+    Tr[i + (size_t)j * k] = u * sc;
+  }
+}
+
+__global__ void finalize_rank(const double* D, int64_t k, int64_t ldd, const double* lam, int r_cap, double tau,
+                              int r_fixed, double* out_eig, int* r_dev, double* trace_dev) {
+  if (threadIdx.x != 0) return;
+  double tr = 0.0;
+  for (int64_t i = 0; i < k; ++i) tr += D[i + i * ldd];
+  int r = 0;
+  if (r_fixed > 0) {
+    r = r_fixed;
+  } else {
+    double cum = 0.0;
+    for (int i = 0; i < r_cap; ++i) {
+      cum += lam[i];
+      if (cum / tr > tau) {
+        r = i + 1;
+        break;
+      }
+    }
+  }
+  for (int i = 0; i < r_cap; ++i) out_eig[i] = lam[i];
+  if (r > 0 && !(lam[r - 1] > 0.0)) r = -r;  // lambda_r <= 0
+  *r_dev = r;
+  *trace_dev = tr;
+}
+
+struct ReduceWs {
+  double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *Dg, *Du, *Du2, *Dl, *trace;
+  unsigned char* piv;
+  int* r;
+  void* tn;
+  size_t tn_bytes, used;
+};
+
+// One layout for the size query (base == nullptr) and the entry point.
+ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
+  Carver c(base);
+  ReduceWs w;
+  w.A = c.take<double>((size_t)k * k);
+  w.d = c.take<double>(k);
+  w.e = c.take<double>(k);
+  w.tau = c.take<double>(k);
+  w.p = c.take<double>(k);
+  w.lam = c.take<double>(r_cap);
+  w.tnorm = c.take<double>(1);
+  w.trace = c.take<double>(1);
+  w.r = c.take<int>(1);
+  w.Z = c.take<double>((size_t)k * r_cap);
+  w.U = c.take<double>((size_t)k * r_cap);
+  w.Dg = c.take<double>((size_t)k * r_cap);
+  w.Du = c.take<double>((size_t)k * r_cap);
+  w.Du2 = c.take<double>((size_t)k * r_cap);
+  w.Dl = c.take<double>((size_t)k * r_cap);
+  w.piv = c.take<unsigned char>((size_t)k * r_cap);
+  w.tn_bytes = tn_workspace(k, r_cap, k, 0);
+  w.tn = c.take<char>(w.tn_bytes);
+  w.used = c.used;
+  return w;
+}
+
+}  // namespace
+}  // namespace dopinf
+
+using namespace dopinf;
+
+DOPINF_API size_t dopinf_reduce_workspace(int64_t k, int r_cap) {
+  if (k < 1 || r_cap < 1) return 0;
+  return carve_reduce(nullptr, k, r_cap).used;
+}
+
+DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed, int r_cap,
+                             int* r_out, double* trace_out, double* eigvals, double* Tr, double* Qhat, void* ws,
+                             size_t ws_bytes, void* stream) {
+  if (!D || k < 1 || ldd < k || r_cap < 1 || r_cap > k || r_fixed > r_cap || !r_out || !trace_out || !eigvals ||
+      !Tr || !Qhat)
+    return DOPINF_E_ARG;
+  if (r_fixed <= 0 && !(energy_target >= 0.0 && energy_target < 1.0)) return DOPINF_E_ARG;
+  if (!ws || ws_bytes < dopinf_reduce_workspace(k, r_cap) || misaligned(ws)) return DOPINF_E_ARG;
+  if ((size_t)k * sizeof(double) > 200 * 1024) return DOPINF_E_UNSUPPORTED;  // back-transform keeps z in smem
+  cudaStream_t st = as_stream(stream);
+  ReduceWs w = carve_reduce(ws, k, r_cap);
+  DOPINF_CUDA(cudaMemcpy2DAsync(w.A, k * sizeof(double), D, ldd * sizeof(double), k * sizeof(double), k,
+                                cudaMemcpyDeviceToDevice, st));
+  for (int64_t j = 0; j + 2 < k; ++j) {
+    const int64_t m = k - j - 1;
+    hh_gen<<<1, EB, 0, st>>>(w.A, k, j, w.d, w.e, w.tau);
+    hh_symv<<<(unsigned)((m + 7) / 8), EB, 0, st>>>(w.A, k, j, w.tau, w.p);
+    hh_rank2<<<(unsigned)((m + R2_COLS - 1) / R2_COLS), EB, 0, st>>>(w.A, k, j, w.tau, w.p);
+  }
+  hh_tail<<<1, 32, 0, st>>>(w.A, k, w.d, w.e, w.tau);
+  DOPINF_TRY(launch_status());
+  tri_multisect<<<(r_cap + 3) / 4, 128, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm);
+  tri_invit<<<(r_cap + 63) / 64, 64, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.Dg, w.Du, w.Du2, w.Dl, w.piv,
+                                             w.Z);
+  tri_orth<<<1, EB, 0, st>>>(k, r_cap, w.lam, w.tnorm, w.Z);
+  const size_t smem = (size_t)k * sizeof(double);
+  if (smem > 48 * 1024) DOPINF_CUDA(cudaFuncSetAttribute(hh_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  hh_back<<<r_cap, EB, smem, st>>>(w.A, k, r_cap, w.tau, w.lam, w.Z, w.U, Tr);
+  DOPINF_TRY(launch_status());
+  DOPINF_TRY(tn_product(Tr, k, D, ldd, DOPINF_F64, k, r_cap, k, 0, 0, Qhat, r_cap, w.tn, w.tn_bytes, st));
+  finalize_rank<<<1, 32, 0, st>>>(D, k, ldd, w.lam, r_cap, energy_target, r_fixed, eigvals, w.r, w.trace);
+  DOPINF_TRY(launch_status());
+  int r_host = 0;
+  double tr_host = 0.0;
+  DOPINF_CUDA(cudaMemcpyAsync(&r_host, w.r, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DOPINF_CUDA(cudaMemcpyAsync(&tr_host, w.trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DOPINF_CUDA(cudaStreamSynchronize(st));
+  *trace_out = tr_host;
+  if (r_host == 0) {
+    *r_out = 0;
+    return DOPINF_E_RANK;
+  }
+  if (r_host < 0) {
+    *r_out = -r_host;
+    return DOPINF_E_RANK;
+  }
+  *r_out = r_host;
+  return DOPINF_OK;
+}

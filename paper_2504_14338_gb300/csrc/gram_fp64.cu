@@ -1,0 +1,190 @@
+// FP64 "TN" product C = A^T B over a long contraction dimension K (the rows of the
+// snapshot matrix), used for the method-of-snapshots Gram D = Q^T Q (Section 3.4,
+// eq. mos_partitioned) and for the OpInf normal equations Dhat^T Dhat, Dhat^T Y (Section 3.5,
+// eq. OpInf_reg).
+//
+// Design: 64 x 64 output tiles, 256 threads with 4 x 4 FP64 accumulators each, K staged
+// through shared memory 16 rows at a time.  K is split across CTAs (the partitioned sum
+// D = sum_i Q_i^T Q_i of the paper, with row blocks as the partitions); every CTA writes its
+// partial tile to the workspace and a second kernel adds the partials in split order, so the
+// result does not depend on scheduling.  With sym = 1 only tiles on or above the diagonal are
+// computed and mirrored.  On GB300 the FP64 pipe (about 1.1 TFLOP/s for the whole chip) and
+// not HBM bounds this kernel: every staged element feeds 64 FMAs.
+#include "common.cuh"
+
+namespace dopinf {
+namespace {
+
+constexpr int TM = 64, TN = 64, BK = 16, NT = 256;
+constexpr int kTargetCtas = 152 * 4;
+
+struct TnPlan {
+  int tiles_m, tiles_n, ntiles, splits;
+  int64_t rows_per_split;
+};
+
+TnPlan make_plan(int64_t K, int64_t M, int64_t N, int sym) {
+  TnPlan p;
+  p.tiles_m = (int)((M + TM - 1) / TM);
+  p.tiles_n = (int)((N + TN - 1) / TN);
+  p.ntiles = sym ? p.tiles_n * (p.tiles_n + 1) / 2 : p.tiles_m * p.tiles_n;
+  if (p.ntiles < 1) p.ntiles = 1;
+  int64_t max_splits = (K + BK * 8 - 1) / (BK * 8);  // at least 128 rows per split
+  if (max_splits < 1) max_splits = 1;
+  int64_t splits = (kTargetCtas + p.ntiles - 1) / p.ntiles;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  int64_t rps = (K + splits - 1) / splits;
+  rps = (rps + BK - 1) / BK * BK;
+  if (rps < BK) rps = BK;
+  p.rows_per_split = rps;
+  p.splits = (int)((K + rps - 1) / rps);
+  if (p.splits < 1) p.splits = 1;
+  return p;
+}
+
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int sym, int& bi, int& bj) {
+  if (sym) {
+    int t = tile, row = 0, len = tiles_n;
+    while (t >= len) {
+      t -= len;
+      ++row;
+      --len;
+    }
+    bi = row;
+    bj = row + t;
+  } else {
+    bi = tile % tiles_m;
+    bj = tile / tiles_m;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) tn_partial(const T* __restrict__ A, int64_t lda,
+                                                 const T* __restrict__ B, int64_t ldb, int64_t K,
+                                                 int64_t M, int64_t N, int64_t rows_per_split,
+                                                 int tiles_m, int tiles_n, int sym, int ntiles,
+                                                 double* __restrict__ part) {
+  __shared__ double As[BK][TM + 1];
+  __shared__ double Bs[BK][TN + 1];
+  int bi, bj;
+  tile_coords(blockIdx.x, tiles_m, tiles_n, sym, bi, bj);
+  const int64_t m0 = (int64_t)bi * TM, n0 = (int64_t)bj * TN;
+  const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t k1 = k0 + rows_per_split < K ? k0 + rows_per_split : K;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int lr = tid & 15, lc = tid >> 4;  // loader: row within the chunk, column group
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int64_t kk = k0; kk < k1; kk += BK) {
+    const int64_t row = kk + lr;
+    const bool rv = row < k1;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int c = lc + 16 * p;
+      const int64_t gm = m0 + c, gn = n0 + c;
+      As[lr][c] = (rv && gm < M) ? (double)A[row + gm * lda] : 0.0;
+      Bs[lr][c] = (rv && gn < N) ? (double)B[row + gn * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < BK; ++r) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[r][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[r][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = part + ((size_t)blockIdx.y * ntiles + blockIdx.x) * (TM * TN);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[(ty + 16 * j) * TM + tx + 16 * i] = acc[i][j];
+}
+
+__global__ void __launch_bounds__(NT) tn_reduce(const double* __restrict__ part, int splits, int ntiles,
+                                                int tiles_m, int tiles_n, int sym, int64_t M, int64_t N,
+                                                int accumulate, double* __restrict__ C, int64_t ldc) {
+  int bi, bj;
+  tile_coords(blockIdx.x, tiles_m, tiles_n, sym, bi, bj);
+  const int e = blockIdx.y * NT + threadIdx.x;  // element of the tile, column-major
+  const int m = e % TM, nn = e / TM;
+  const int64_t gm = (int64_t)bi * TM + m, gn = (int64_t)bj * TN + nn;
+  if (gm >= M || gn >= N) return;
+  double s = 0.0;
+  for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * ntiles + blockIdx.x) * (TM * TN) + e];
+  if (accumulate) s += C[gm + gn * ldc];
+  C[gm + gn * ldc] = s;
+  if (sym && bi != bj) C[gn + gm * ldc] = s;
+}
+
+}  // namespace
+
+size_t tn_workspace(int64_t K, int64_t M, int64_t N, int sym) {
+  TnPlan p = make_plan(K, M, N, sym);
+  Carver c(nullptr);
+  c.take<double>((size_t)p.splits * p.ntiles * TM * TN);
+  return c.used;
+}
+
+int tn_product(const void* A, int64_t lda, const void* B, int64_t ldb, int dtype, int64_t K, int64_t M,
+               int64_t N, int sym, int accumulate, double* C, int64_t ldc, void* ws, size_t ws_bytes,
+               cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DOPINF_OK;
+  if (K < 0 || !C || ldc < M || (K > 0 && (!A || !B || lda < K || ldb < K))) return DOPINF_E_ARG;
+  if (sym && (A != B || M != N || lda != ldb)) return DOPINF_E_ARG;
+  TnPlan p = make_plan(K, M, N, sym);
+  if (!ws || ws_bytes < tn_workspace(K, M, N, sym) || misaligned(ws)) return DOPINF_E_ARG;
+  Carver cv(ws);
+  double* part = cv.take<double>((size_t)p.splits * p.ntiles * TM * TN);
+  dim3 grid(p.ntiles, p.splits);
+  if (dtype == DOPINF_F64)
+    tn_partial<double><<<grid, NT, 0, st>>>(static_cast<const double*>(A), lda, static_cast<const double*>(B),
+                                            ldb, K, M, N, p.rows_per_split, p.tiles_m, p.tiles_n, sym,
+                                            p.ntiles, part);
+  else if (dtype == DOPINF_F32)
+    tn_partial<float><<<grid, NT, 0, st>>>(static_cast<const float*>(A), lda, static_cast<const float*>(B),
+                                           ldb, K, M, N, p.rows_per_split, p.tiles_m, p.tiles_n, sym,
+                                           p.ntiles, part);
+  else
+    return DOPINF_E_ARG;
+  DOPINF_TRY(launch_status());
+  tn_reduce<<<dim3(p.ntiles, TM * TN / NT), NT, 0, st>>>(part, p.splits, p.ntiles, p.tiles_m, p.tiles_n,
+                                                         sym, M, N, accumulate, C, ldc);
+  return launch_status();
+}
+
+}  // namespace dopinf
+
+using namespace dopinf;
+
+DOPINF_API size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode) {
+  (void)dtype;
+  if (mode != DOPINF_GRAM_FP64) return 0;
+  return tn_workspace(n, k, k, 1);
+}
+
+DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
+                           int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
+                           void* stream) {
+  if (n < 0 || k < 1 || ldq < (n > 1 ? n : 1) || ldd < k || !D || (n > 0 && !Q)) return DOPINF_E_ARG;
+  if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
+  if (mode != DOPINF_GRAM_FP64) return DOPINF_E_UNSUPPORTED;
+  if (n == 0) {
+    if (accumulate) return DOPINF_OK;
+    return cuda_status(cudaMemset2DAsync(D, ldd * sizeof(double), 0, k * sizeof(double), k,
+                                         as_stream(stream)));
+  }
+  return tn_product(Q, ldq, Q, ldq, dtype, n, k, k, 1, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
+}

@@ -1,0 +1,236 @@
+"""Thin Python binding of the libdopinf C ABI (include/dopinf.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA library.  Device
+memory, workspaces and streams come from PyTorch; tensors are passed by data pointer.  The
+functions keep the C names.  Importing this module loads libdopinf.so and raises if it is
+missing - there is no fallback.
+
+Layout convention: the snapshot matrix is column-major, i.e. a torch tensor of shape (n, k)
+with strides (1, ldq); ``snapshot_matrix(n, k)`` allocates one, and ``QT.t()`` of a row-major
+(k, n) tensor is one.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdopinf.so")
+
+OK, E_ARG, E_CUDA, E_NONFINITE, E_RANK, E_NO_STABLE, E_UNSUPPORTED = 0, -1, -2, -4, -6, -7, -9
+FLAG_NONFINITE, FLAG_ZERO_SCALE = 1, 2
+F64, F32 = 0, 1
+CENTER, SCALE = 1, 2
+GRAM_FP64, GRAM_BF16X3 = 0, 1
+DISCRETE, CONTINUOUS_RK4 = 0, 1
+
+_c_i64 = ctypes.c_int64
+_c_p = ctypes.c_void_p
+_c_sz = ctypes.c_size_t
+
+
+class DopinfError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__("%s failed: %d (%s)" % (fn, status, status_string(status)))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdopinf.so is not built (run __graft_entry__.build()); "
+                          "the dOpInf hot path has no non-CUDA fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "dopinf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "dopinf_transform_workspace": (_c_sz, [_c_i64, ctypes.c_int]),
+        "dopinf_transform": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int,
+                                            ctypes.POINTER(_c_i64), ctypes.c_uint, _c_p, _c_p, _c_p,
+                                            _c_p, _c_sz, _c_p]),
+        "dopinf_gram_workspace": (_c_sz, [_c_i64, _c_i64, ctypes.c_int, ctypes.c_int]),
+        "dopinf_gram": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int,
+                                       ctypes.c_int, _c_p, _c_i64, _c_p, _c_sz, _c_p]),
+        "dopinf_reduce_workspace": (_c_sz, [_c_i64, ctypes.c_int]),
+        "dopinf_reduce": (ctypes.c_int, [_c_p, _c_i64, _c_i64, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double), _c_p, _c_p, _c_p, _c_p,
+                                         _c_sz, _c_p]),
+        "dopinf_learn_workspace": (_c_sz, [ctypes.c_int, _c_i64, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "dopinf_learn": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, _c_i64, ctypes.c_double, _c_p, _c_p, _c_p,
+                                        ctypes.POINTER(ctypes.c_int), _c_p, _c_p, _c_sz, _c_p]),
+        "dopinf_rollout": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_p, _c_i64, ctypes.c_int,
+                                          ctypes.c_double, _c_p, _c_p, _c_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_string(status):
+    return lib.dopinf_status_string(int(status)).decode()
+
+
+def _check(fn, status, allowed=(OK,)):
+    if status not in allowed:
+        raise DopinfError(fn, status)
+    return status
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Workspace:
+    """Reusable device workspace (256-byte aligned) grown on demand."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes):
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.buf.data_ptr()) % 256
+        return self.buf[off:off + nbytes]
+
+
+_default_ws = {}
+
+
+def _ws(nbytes, ws, device):
+    if ws is None:
+        ws = _default_ws.setdefault(str(device), Workspace(device))
+    buf = ws.get(nbytes)
+    return buf, nbytes
+
+
+def snapshot_matrix(n, k, dtype=torch.float64, device="cuda"):
+    """Column-major (n, k) tensor: snapshot t is contiguous."""
+    return torch.empty(k, n, dtype=dtype, device=device).t()
+
+
+def _colmajor(Q):
+    n, k = Q.shape
+    if Q.stride(0) != 1 or (k > 1 and Q.stride(1) < max(n, 1)):
+        raise ValueError("expected a column-major (n, k) tensor with strides (1, ldq >= n)")
+    return n, k, Q.stride(1) if k > 1 else max(n, 1)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError("snapshot data must be float64 or float32")
+
+
+def dopinf_transform(Q, var_row_offsets, flags=CENTER | SCALE, dev_flags=None, ws=None, stream=None):
+    """Step II in place on Q; returns (row_mean, var_scale, dev_flags)."""
+    n, k, ldq = _colmajor(Q)
+    offs = (_c_i64 * len(var_row_offsets))(*[int(v) for v in var_row_offsets])
+    n_vars = len(var_row_offsets) - 1
+    mean = torch.empty(n, dtype=torch.float64, device=Q.device)
+    scale = torch.empty(n_vars, dtype=torch.float64, device=Q.device)
+    if dev_flags is None:
+        dev_flags = torch.zeros(1, dtype=torch.int32, device=Q.device)
+    nb = lib.dopinf_transform_workspace(n, n_vars)
+    buf, nb = _ws(nb, ws, Q.device)
+    _check("dopinf_transform", lib.dopinf_transform(_ptr(Q), _dtype_code(Q), n, k, ldq, n_vars, offs, flags,
+                                                    _ptr(mean), _ptr(scale), _ptr(dev_flags), _ptr(buf), nb,
+                                                    _stream(stream)))
+    return mean, scale, dev_flags
+
+
+def dopinf_gram(Q, mode=GRAM_FP64, D=None, accumulate=False, ws=None, stream=None):
+    """Step III Gram D = Q^T Q (k x k FP64); with accumulate, D += Q^T Q."""
+    n, k, ldq = _colmajor(Q)
+    if D is None:
+        D = torch.zeros(k, k, dtype=torch.float64, device=Q.device)
+    nb = lib.dopinf_gram_workspace(n, k, _dtype_code(Q), mode)
+    buf, nb = _ws(nb, ws, Q.device)
+    # D is symmetric, so its row-major storage is its column-major storage
+    _check("dopinf_gram", lib.dopinf_gram(_ptr(Q), _dtype_code(Q), n, k, ldq, mode, int(accumulate), _ptr(D),
+                                          D.stride(0), _ptr(buf), nb, _stream(stream)))
+    return D
+
+
+def dopinf_reduce(D, r_cap, energy_target=0.9996, r_fixed=0, ws=None, stream=None):
+    """Step III eigensolve/projection.  Returns dict(r, trace, eigvals, Tr (k x r_cap), Qhat (r_cap x k)).
+
+    Qhat is returned as an (r_cap, k) tensor whose column t is the reduced snapshot t.
+    """
+    k = D.shape[0]
+    dev = D.device
+    eig = torch.empty(r_cap, dtype=torch.float64, device=dev)
+    Tr = torch.empty(r_cap, k, dtype=torch.float64, device=dev).t()       # k x r_cap column-major
+    Qhat = torch.empty(k, r_cap, dtype=torch.float64, device=dev).t()     # r_cap x k column-major
+    r = ctypes.c_int(0)
+    tr = ctypes.c_double(0.0)
+    nb = lib.dopinf_reduce_workspace(k, r_cap)
+    buf, nb = _ws(nb, ws, dev)
+    st = lib.dopinf_reduce(_ptr(D), k, D.stride(0), float(energy_target), int(r_fixed), int(r_cap),
+                           ctypes.byref(r), ctypes.byref(tr), _ptr(eig), _ptr(Tr), _ptr(Qhat), _ptr(buf), nb,
+                           _stream(stream))
+    _check("dopinf_reduce", st)
+    return dict(r=r.value, trace=tr.value, eigvals=eig, Tr=Tr, Qhat=Qhat, status=st)
+
+
+def dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=DISCRETE, dt=1.0, max_growth=1.2, ws=None,
+                 stream=None, allow_no_stable=True):
+    """Step IV grid search.  Qhat: (r_max, k) column-major.  Returns a dict of results."""
+    r_max, k = Qhat.shape
+    if Qhat.stride(0) != 1:
+        raise ValueError("Qhat must be column-major (r_max, k)")
+    ldqh = Qhat.stride(1)
+    dev = Qhat.device
+    rl = (ctypes.c_int * len(r_list))(*[int(r) for r in r_list])
+    b1 = (ctypes.c_double * len(beta1))(*[float(b) for b in beta1])
+    b2 = (ctypes.c_double * len(beta2))(*[float(b) for b in beta2])
+    n_cand = len(r_list) * len(beta1) * len(beta2)
+    err = torch.empty(n_cand, dtype=torch.float64, device=dev)
+    gro = torch.empty(n_cand, dtype=torch.float64, device=dev)
+    cst = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    d_max = max(r + r * (r + 1) // 2 + 1 for r in r_list)
+    O_best = torch.zeros(d_max, r_max, dtype=torch.float64, device=dev).t()  # r_max x d_max column-major
+    best = ctypes.c_int(-1)
+    nb = lib.dopinf_learn_workspace(r_max, k, rl, len(r_list), len(beta1), len(beta2))
+    buf, nb = _ws(nb, ws, dev)
+    st = lib.dopinf_learn(_ptr(Qhat), r_max, k, ldqh, rl, len(r_list), b1, len(beta1), b2, len(beta2), int(mode),
+                          float(dt), int(n_steps), float(max_growth), _ptr(err), _ptr(gro), _ptr(cst),
+                          ctypes.byref(best), _ptr(O_best), _ptr(buf), nb, _stream(stream))
+    _check("dopinf_learn", st, (OK, E_NO_STABLE) if allow_no_stable else (OK,))
+    out = dict(train_err=err, growth=gro, status=cst, best=best.value, O_best=O_best, code=st)
+    if best.value >= 0:
+        nb12 = len(beta1) * len(beta2)
+        r = int(r_list[best.value // nb12])
+        out.update(r=r, beta1=float(beta1[(best.value % nb12) // len(beta2)]),
+                   beta2=float(beta2[best.value % len(beta2)]),
+                   O=O_best[:r, :r + r * (r + 1) // 2 + 1])
+    return out
+
+
+def dopinf_rollout(O, q0, n_steps, mode=DISCRETE, dt=1.0, stream=None):
+    """Rollout of one ROM.  O: (r, d) column-major view; returns (Qtilde (n_steps x r), finite)."""
+    r, d = O.shape
+    if O.stride(0) != 1:
+        raise ValueError("O must be column-major (r, d)")
+    Qt = torch.full((n_steps, r), float("nan"), dtype=torch.float64, device=O.device)
+    fin = torch.zeros(1, dtype=torch.int32, device=O.device)
+    q0 = q0.contiguous()
+    _check("dopinf_rollout", lib.dopinf_rollout(_ptr(O), r, O.stride(1) if d > 1 else r, _ptr(q0), int(n_steps),
+                                                int(mode), float(dt), _ptr(Qt), _ptr(fin), _stream(stream)))
+    return Qt, fin

@@ -4,16 +4,17 @@ checker; holds none of the method's arithmetic).
 The paper's Navier-Stokes snapshots and the detonation data are not available, so every
 input is generated from a seeded quadratic dynamical system that is lifted to n rows:
 
-* generating system (dimension r_true): x' = A x + H(x, x) + c.  A is a Gaussian matrix
-  (entries N(0, 1/r)) shifted so that the largest eigenvalue of its symmetric part is
-  -0.1, which bounds every trajectory together with an energy-preserving H
+* generating system (dimension r_true): x' = A x + H(x, x) + c.  A = omega (G - G^T) / (2 sqrt r)
+  - 0.1 I with G Gaussian: a rotation with frequencies of order omega whose symmetric part
+  is exactly -0.1 I, which bounds every trajectory together with an energy-preserving H
   (x^T H(x, x) = 0 for all x; H = S - sym3(S) for a random S symmetric in its last two
   indices).  c has entries N(0, 0.01) (variance 0.01).  The system is integrated with
-  classical RK4 at step dt from x0 ~ N(0, 1), every step being one snapshot;
+  classical RK4 at step dt from x0 ~ N(0, 1); every stride-th state is one snapshot, so
+  the snapshot spacing is dt * stride;
 * lift: Q = L X + noise, L an n x r_true matrix with orthonormal columns (QR of a
   Gaussian), optionally re-shaped so that the squared singular values of L X decay as
-  i^-p; noise is Gaussian with the stated variance; each variable block of rows is
-  multiplied by its own scale factor.
+  i^-p; the noise is Gaussian with standard deviation noise_rel times the RMS entry of
+  L X; each variable block of rows is multiplied by its own scale factor.
 
 Named workloads (sizes of the paper's example and of the GB300 benchmark set):
   small     n = 2 x 2048,   k = 200,  r_true = 6
@@ -33,7 +34,10 @@ class Workload:
     k: int
     r_true: int
     dt: float = 1e-3
-    noise_var: float = 1e-4
+    stride: int = 10
+    omega: float = 2 * np.pi
+    h_scale: float = 1.0
+    noise_rel: float = 1e-4
     var_scales: tuple = ()
     decay: float = 0.0          # 0: plain lift; p > 0: squared singular values ~ i^-p
     dtype: str = "f64"
@@ -49,6 +53,11 @@ class Workload:
     @property
     def n(self):
         return self.n_vars * self.n_per_var
+
+    @property
+    def snap_dt(self):
+        """Time between snapshots (the step of continuous-mode rollouts)."""
+        return self.dt * self.stride
 
     def var_row_offsets(self):
         return np.arange(self.n_vars + 1, dtype=np.int64) * self.n_per_var
@@ -66,7 +75,7 @@ WORKLOADS = {
                          r_list=(10, 20, 30), n_beta1=8, n_beta2=8,
                          beta1_range=(-10.0, 0.0), beta2_range=(-4.0, 4.0),
                          n_steps=5000, mode="continuous", seed=1235),
-    "rdre": Workload("rdre", 8, 1_500_000, 2000, 120, noise_var=1e-12, decay=3.0,
+    "rdre": Workload("rdre", 8, 1_500_000, 2000, 120, noise_rel=1e-6, decay=3.0,
                      dtype="f32", r_list=(100,), seed=1236),
     "paper": Workload("paper", 2, 146_339, 600, 12, r_list=(10,), n_beta1=8, n_beta2=8,
                       beta1_range=(-10.0, 0.0), beta2_range=(-4.0, 4.0), n_steps=1200,
@@ -82,12 +91,11 @@ def logspace(lo, hi, num):
     return 10.0 ** e
 
 
-def quadratic_system(r, rng):
+def quadratic_system(r, rng, omega=2 * np.pi, h_scale=1.0):
     """(A, H3, c): A (r, r), H3 (r, r, r) energy preserving and symmetric in (j, k), c (r,)."""
-    A = rng.standard_normal((r, r)) / np.sqrt(r)
-    mu = np.linalg.eigvalsh(0.5 * (A + A.T)).max()
-    A = A - (mu + 0.1) * np.eye(r)
-    S = rng.standard_normal((r, r, r)) / r
+    G = rng.standard_normal((r, r))
+    A = omega * (G - G.T) / (2.0 * np.sqrt(r)) - 0.1 * np.eye(r)
+    S = rng.standard_normal((r, r, r)) * (h_scale / r)
     S = 0.5 * (S + S.transpose(0, 2, 1))
     sym = (S + S.transpose(0, 2, 1) + S.transpose(1, 0, 2) + S.transpose(1, 2, 0)
            + S.transpose(2, 0, 1) + S.transpose(2, 1, 0)) / 6.0
@@ -111,26 +119,27 @@ def _field(A, H3, c, x):
     return A @ x + np.einsum("ijk,j,k->i", H3, x, x) + c
 
 
-def integrate_rk4(A, H3, c, x0, dt, k):
-    """k states (x0 included) of the generating system under classical RK4."""
+def integrate_rk4(A, H3, c, x0, dt, k, stride=1):
+    """k states (x0 included, every stride-th RK4 step) of the generating system."""
     X = np.empty((A.shape[0], k))
     x = np.array(x0, dtype=np.float64)
     for t in range(k):
         X[:, t] = x
-        k1 = _field(A, H3, c, x)
-        k2 = _field(A, H3, c, x + 0.5 * dt * k1)
-        k3 = _field(A, H3, c, x + 0.5 * dt * k2)
-        k4 = _field(A, H3, c, x + dt * k3)
-        x = x + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        for _ in range(stride):
+            k1 = _field(A, H3, c, x)
+            k2 = _field(A, H3, c, x + 0.5 * dt * k1)
+            k3 = _field(A, H3, c, x + 0.5 * dt * k2)
+            k4 = _field(A, H3, c, x + dt * k3)
+            x = x + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
     return X
 
 
 def trajectory(w: Workload):
     """Reduced trajectory X (r_true, k) and the generating system of a workload."""
     rng = np.random.default_rng(w.seed)
-    A, H3, c = quadratic_system(w.r_true, rng)
+    A, H3, c = quadratic_system(w.r_true, rng, w.omega, w.h_scale)
     x0 = rng.standard_normal(w.r_true)
-    X = integrate_rk4(A, H3, c, x0, w.dt, w.k)
+    X = integrate_rk4(A, H3, c, x0, w.dt, w.k, w.stride)
     return X, (A, H3, c)
 
 
@@ -156,8 +165,9 @@ def snapshots_numpy(w: Workload):
     rng = np.random.default_rng(w.seed + 1_000_003)
     L = lift_matrix_small(w, X, rng)
     Q = L @ X
-    if w.noise_var > 0:
-        Q += rng.standard_normal(Q.shape) * np.sqrt(w.noise_var)
+    if w.noise_rel > 0:
+        rms = np.linalg.norm(Q) / np.sqrt(Q.size)
+        Q += rng.standard_normal(Q.shape) * (w.noise_rel * rms)
     if w.var_scales:
         for j, s in enumerate(w.var_scales):
             Q[j * w.n_per_var:(j + 1) * w.n_per_var, :] *= s
@@ -179,7 +189,9 @@ def snapshots_torch(w: Workload, device, col_major=True):
     G = torch.randn(w.n, w.r_true, generator=g, device=device, dtype=torch.float64)
     L, _ = torch.linalg.qr(G)
     del G
-    M = torch.from_numpy(X if w.decay <= 0 else _decay_shaper(X, w.decay) @ X).to(device)
+    Mn = X if w.decay <= 0 else _decay_shaper(X, w.decay) @ X
+    M = torch.from_numpy(Mn).to(device)
+    noise_std = w.noise_rel * np.linalg.norm(Mn) / np.sqrt(w.n * w.k)  # ||L M||_F = ||M||_F
     dt = torch.float32 if w.dtype == "f32" else torch.float64
     QT = torch.empty(w.k, w.n, device=device, dtype=dt)
     sc = torch.ones(w.n, device=device, dtype=torch.float64)
@@ -190,8 +202,8 @@ def snapshots_torch(w: Workload, device, col_major=True):
     for t0 in range(0, w.k, step):
         t1 = min(w.k, t0 + step)
         blk = (L @ M[:, t0:t1]).T
-        if w.noise_var > 0:
+        if w.noise_rel > 0:
             blk += torch.randn(blk.shape, generator=g, device=device,
-                               dtype=torch.float64) * (w.noise_var ** 0.5)
+                               dtype=torch.float64) * noise_std
         QT[t0:t1] = (blk * sc).to(dt)
     return QT

@@ -1,0 +1,109 @@
+"""Parity at the benchmark's full size (2D step-flow shape: n = 1.2M rows, k = 600,
+r in {10, 20, 30}, 8 x 8 grid, 5000-step RK4), in the launch configuration bench.py times,
+on outputs the FP64 oracle can compute one by one: sampled rows of the transform, sampled
+Gram entries, the whole k x k eigenproblem, and a sample of the learn candidates."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dopinf_oracle as O
+from paper_2504_14338_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def run():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2504_14338_gb300 import dopinf as dp
+    w = synth.WORKLOADS["stepflow"]
+    QT = synth.snapshots_torch(w, torch.device("cuda"))
+    Q = QT.t()
+    rng = np.random.default_rng(0)
+    npv = w.n_per_var
+    rows = np.unique(np.concatenate([rng.choice(w.n, 3000, replace=False),
+                                     [0, npv - 1, npv, 2 * npv - 1, 2 * npv, w.n - 1]]))
+    raw = Q[torch.from_numpy(rows).cuda()].cpu().numpy()
+    ws = dp.Workspace("cuda")
+    mean, scale, flags = dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
+    D = dp.dopinf_gram(Q, ws=ws)
+    red = dp.dopinf_reduce(D, r_cap=max(w.r_list), r_fixed=max(w.r_list), ws=ws)
+    b1, b2 = w.beta1s(), w.beta2s()
+    res = dp.dopinf_learn(red["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=dp.CONTINUOUS_RK4,
+                          dt=w.snap_dt, ws=ws)
+    torch.cuda.synchronize()
+    return dict(dp=dp, w=w, Q=Q, rows=rows, raw=raw, mean=mean, scale=scale, flags=flags, D=D, red=red,
+                res=res, b1=b1, b2=b2)
+
+
+def test_transform_sampled_rows_bit_exact(run):
+    w, rows, raw = run["w"], run["rows"], run["raw"]
+    _, rmean, _, _ = O.transform(raw, [0, len(rows)], scale=False)
+    assert np.array_equal(run["mean"].cpu().numpy()[rows], rmean)
+    scale = run["scale"].cpu().numpy()
+    var = rows // w.n_per_var
+    centred, _, _, _ = O.transform(raw, [0, len(rows)], scale=False)
+    expect = centred / scale[var][:, None]
+    got = run["Q"][torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.array_equal(got, expect)
+    # the scale is the block's max |centred value|: every block then peaks at exactly 1
+    Q = run["Q"]
+    for j in range(w.n_vars):
+        blk = Q[j * w.n_per_var:(j + 1) * w.n_per_var]
+        assert float(blk.abs().max()) == 1.0
+    assert int(run["flags"].item()) == 0
+
+
+def test_gram_sampled_entries(run):
+    w, Q, D = run["w"], run["Q"], run["D"].cpu().numpy()
+    rng = np.random.default_rng(1)
+    cols = np.unique(np.concatenate([rng.choice(w.k, 24, replace=False), [0, 63, 64, w.k - 1]]))
+    Qc = Q[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    ref = O.gram(Qc)
+    got = D[np.ix_(cols, cols)]
+    bound = 4 * np.sqrt(w.n) * EPS * np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    assert np.all(np.abs(got - ref) <= bound)
+    assert np.array_equal(D, D.T)
+
+
+def test_reduce_full_eigenproblem(run):
+    w, D, red = run["w"], run["D"].cpu().numpy(), run["red"]
+    r = max(w.r_list)
+    ref = O.reduce(D, r_fixed=r)
+    lam_ref = ref["lam"]
+    lam = red["eigvals"].cpu().numpy()
+    assert np.all(np.abs(lam - lam_ref[:r]) <= 1e-10 * lam_ref[:r] + 8 * w.k * EPS * lam_ref[0])
+    gaps = np.abs(np.diff(lam_ref))
+    Qh, Qh_ref = red["Qhat"].cpu().numpy(), ref["Qhat"]
+    for j in range(r):
+        gap = min(gaps[j - 1] if j else np.inf, gaps[j])
+        err = np.linalg.norm(Qh[j] - Qh_ref[j]) / np.linalg.norm(Qh_ref[j])
+        assert err <= 1e-10 + 1e3 * w.k * EPS * lam_ref[0] / gap, (j, err)
+
+
+def test_learn_sampled_candidates(run):
+    w, res, red = run["w"], run["res"], run["red"]
+    D = run["D"].cpu().numpy()
+    Qh_ref = O.reduce(D, r_fixed=max(w.r_list))["Qhat"]
+    st = res["status"].cpu().numpy()
+    err = res["train_err"].cpu().numpy()
+    nb = len(run["b1"]) * len(run["b2"])
+    rng = np.random.default_rng(2)
+    valid = np.nonzero(st == 0)[0]
+    assert len(valid) >= 1 and res["best"] >= 0
+    sample = set(rng.choice(len(st), 4, replace=False).tolist()) | {res["best"]}
+    sample |= set(rng.choice(valid, min(2, len(valid)), replace=False).tolist())
+    for c in sorted(sample):
+        r = w.r_list[c // nb]
+        b1 = run["b1"][(c % nb) // len(run["b2"])]
+        b2 = run["b2"][c % len(run["b2"])]
+        ref = O.learn(Qh_ref, [r], [b1], [b2], w.n_steps, mode="continuous", dt=w.snap_dt)
+        if ref["valid"][0] and st[c] == 0:
+            # FP64 on both sides; the learned operators inherit cond(G + reg) * eps
+            assert abs(err[c] - ref["train_err"][0]) <= 1e-6 * ref["train_err"][0], (c, err[c], ref["train_err"][0])
+        elif min(b1, b2) >= 1e-6:
+            assert ref["valid"][0] == (st[c] == 0), (c, st[c], ref["growth"][0])

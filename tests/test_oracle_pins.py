@@ -229,14 +229,14 @@ def test_discrete_opinf_recovers_known_quadratic_map():
 def test_continuous_opinf_recovers_rk4_system_to_fd_order():
     # continuous mode on RK4 data of a known system: central differences are second order,
     # so the learned right-hand side matches the true one to O(dt^2).
-    w = synth.Workload("pin", 1, 50, 400, 3, dt=1e-2, noise_var=0.0, seed=7)
+    w = synth.Workload("pin", 1, 50, 400, 3, dt=1e-3, stride=1, noise_rel=0.0, seed=7)
     X, (A, H3, c) = synth.trajectory(w)
     rng = np.random.default_rng(8)
     Phi, _ = np.linalg.qr(rng.standard_normal((50, 3)))
     Q = Phi @ X
     red = O.reduce(O.gram(Q), r_fixed=3)
     R = X @ red["Tr"]
-    Dhat, Y = O.learning_data(red["Qhat"], 3, mode="continuous", dt=w.dt)
+    Dhat, Y = O.learning_data(red["Qhat"], 3, mode="continuous", dt=w.snap_dt)
     G, B = O.normal_equations(Dhat, Y)
     Op, ok = O.solve_cholesky(G, B, O.regulariser(3, 1e-14, 1e-14))
     assert ok
