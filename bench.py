@@ -40,8 +40,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--stage", default="all", choices=["all", "gram"],
-                   help="gram: time only the Gram of the transformed matrix (for profiling)")
+    p.add_argument("--stage", default="all", choices=["all", "gram", "learn"],
+                   help="gram / learn: time only that stage (for profiling)")
     p.add_argument("--n-per-var", type=int, default=0, help="override rows per variable (smaller case)")
     return p.parse_args()
 
@@ -208,6 +208,23 @@ def main():
         if rank == 0:
             print(json.dumps({"stage": "gram", "n": w.n, "k": w.k, "ms": ms,
                               "tflops": w.n * w.k * (w.k + 1) / ms / 1e9}), flush=True)
+        return
+    if args.stage == "learn":
+        dp.dopinf_transform(Q, offs, ws=ws)
+        red = dp.dopinf_reduce(dp.dopinf_gram(Q, ws=ws), r_cap=r_max, r_fixed=r_max, ws=ws)
+        times = []
+        for i in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = dp.dopinf_learn(red["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode, dt=w.snap_dt, ws=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        st = res["status"].cpu().numpy()
+        if rank == 0:
+            print(json.dumps({"stage": "learn", "ms": float(np.mean(times)), "best": res["best"],
+                              "valid": int((st == 0).sum()), "n_cand": int(st.size)}), flush=True)
         return
 
     def step(record=False):

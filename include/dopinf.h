@@ -41,6 +41,7 @@ enum dopinf_status {
   DOPINF_E_NONFINITE = -4,    /* NaN or Inf found in the data */
   DOPINF_E_RANK = -6,         /* lambda_r <= 0, or the energy target is not reached by r_cap */
   DOPINF_E_NO_STABLE = -7,    /* no (r, beta1, beta2) candidate is finite and bounded */
+  DOPINF_E_TIMEOUT = -8,      /* a bounded wait inside a tensor-core kernel expired */
   DOPINF_E_UNSUPPORTED = -9   /* valid request this build does not implement */
 };
 
@@ -55,7 +56,7 @@ enum dopinf_dtype { DOPINF_F64 = 0, DOPINF_F32 = 1 };
 
 enum dopinf_gram_mode {
   DOPINF_GRAM_FP64 = 0,      /* FP64 FMA over every row (the plain path) */
-  DOPINF_GRAM_BF16X3 = 1     /* split precision on the tensor cores (see dopinf_gram) */
+  DOPINF_GRAM_BF16X4 = 1     /* two BF16 slices per value, four tensor-core products (see dopinf_gram) */
 };
 
 enum dopinf_rom_mode {
@@ -71,7 +72,7 @@ const char* dopinf_status_string(int status);
  * block by the largest |centred value| of the block.
  *
  * Q            in/out, n x k, element type dtype, leading dimension ldq >= n (elements).
- * n_vars       number of variable blocks (1..1024).
+ * n_vars       number of variable blocks (1..64).
  * var_row_offsets host, n_vars + 1 nondecreasing row offsets, [0] = 0, [n_vars] = n.
  * flags        DOPINF_CENTER | DOPINF_SCALE.
  * row_mean     out, n doubles: mean_i = (sum_t Q[i,t], summed in t order in FP64) / k.
@@ -92,15 +93,28 @@ int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
 
 /* ------------------------------------------------------------------------------------
  * Step III Gram matrix (eq. mos_partitioned): D = Q^T Q, k x k FP64, column-major,
- * leading dimension ldd >= k, both triangles written.  accumulate = 1 adds Q^T Q to D
- * (row blocks of one snapshot matrix, the paper's partitioned sum).
+ * leading dimension ldd >= k, both triangles written (D is exactly symmetric).
+ * accumulate = 1 adds Q^T Q to D (row blocks of one snapshot matrix, the paper's
+ * partitioned sum).  Results are run-to-run bit-reproducible in both modes.
  *
  * DOPINF_GRAM_FP64: Q is FP64 or FP32 (promoted exactly); FP64 products and sums over row
- *   chunks; the chunk partials are added in a fixed order, so the result is run-to-run
- *   bit-reproducible.
- * Workspace: dopinf_gram_workspace(n, k, dtype, mode) bytes.
+ *   chunks; the chunk partials are added in a fixed order.  Asynchronous.
+ * DOPINF_GRAM_BF16X4: each value is split as x = h + l + e, h = bf16(x), l = bf16(x - h),
+ *   and D ~= H^T H + H^T L + L^T H + L^T L on the tcgen05 tensor cores: FP32 accumulation
+ *   over 64-row chunks, a compensated FP32 (TwoSum) running sum per work unit, FP64 sum of
+ *   the units (|e| <= 2^-17 |x|).  Requires k <= 65535.  Synchronises the stream; returns
+ *   DOPINF_E_TIMEOUT if an internal bounded wait expired (D is then not valid).
+ * Workspace: dopinf_gram_workspace(n, k, dtype, mode) bytes (BF16X4: 4 n k bytes of
+ *   slices plus the per-unit FP64 partial tiles).
  * ------------------------------------------------------------------------------------ */
 size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode);
+/* Tuning of DOPINF_GRAM_BF16X4: rows summed by one FP32 tensor-memory accumulator before it
+ * is added to the compensated (TwoSum) running sum (rounded up to a multiple of 64; default
+ * 64).  The tensor core's FP32 accumulation rounds toward zero by about half an ulp per MMA,
+ * so longer chunks trade accuracy (a relative bias growing with the chunk) for fewer drains.
+ * rows <= 0 only queries.  Returns the previous value.  Process-wide; not thread-safe against
+ * concurrent dopinf_gram calls. */
+int64_t dopinf_tune_gram_chunk(int64_t rows);
 int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
                 int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
                 void* stream);
@@ -156,6 +170,10 @@ int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target,
  * Synchronises the stream.  Returns DOPINF_E_NO_STABLE if no candidate is valid.
  * Workspace: dopinf_learn_workspace(...) bytes.
  * ------------------------------------------------------------------------------------ */
+/* Tuning of dopinf_learn: preferred CTAs (1, 2, 4 or 8) of the thread-block cluster that rolls
+ * out one candidate of r >= 16 (default 4); other values only query.  Returns the previous
+ * value.  Process-wide. */
+int dopinf_tune_learn_cluster(int cluster);
 size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1,
                               int n_b2);
 int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list,

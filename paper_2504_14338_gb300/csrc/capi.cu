@@ -9,7 +9,10 @@ DOPINF_API const char* dopinf_status_string(int status) {
     case DOPINF_E_NONFINITE: return "non-finite value in the data";
     case DOPINF_E_RANK: return "reduced dimension exceeds the numerical rank or energy target not reached";
     case DOPINF_E_NO_STABLE: return "no finite, bounded regularisation candidate";
+    case DOPINF_E_TIMEOUT: return "a bounded wait inside a GPU kernel expired";
     case DOPINF_E_UNSUPPORTED: return "request not supported by this build";
     default: return "unknown status";
   }
 }
+
+DOPINF_API int64_t dopinf_tune_gram_chunk(int64_t rows) { return dopinf::gram_tc_set_chunk_rows(rows); }

@@ -58,33 +58,51 @@ int tn_product(const void* A, int64_t lda, const void* B, int64_t ldb, int dtype
                int64_t M, int64_t N, int sym, int accumulate, double* C, int64_t ldc, void* ws,
                size_t ws_bytes, cudaStream_t st);
 
+// Split-precision Gram on the tensor cores (gram_tc.cu); synchronises the stream.
+size_t gram_tc_workspace(int64_t n, int64_t k);
+int64_t gram_tc_set_chunk_rows(int64_t rows);
+int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
+            void* ws, size_t ws_bytes, cudaStream_t st);
+
 // ---------------------------------------------------------------------------------------
-// Batched ROM rollouts (rollout.cu): one CTA per candidate.
+// Batched ROM rollouts (rollout.cu): one thread-block cluster per candidate.
 // ---------------------------------------------------------------------------------------
-struct RolloutArgs {
-  const double* O;      // candidate c's operator at O + c * o_stride, column-major r x d, ld ldo
-  int64_t o_stride, ldo;
+struct RolloutCand {
+  const double* O;      // r x d column-major operator [A | H | c], leading dimension ldo
+  int64_t ldo;
   int r, d;
+  int cand;             // index into the per-candidate outputs
+  const double* mu;     // temporal mean of the reference data (r), metrics runs only
+  const double* denom;  // max_{t<k,i} |qhat - mu|, metrics runs only
+};
+
+struct RolloutBatch {
+  const RolloutCand* cands;  // device table of n_cand candidates, or nullptr to use `one`
+  RolloutCand one;
+  int n_cand, r_max, d_max, rc_max;
   int mode;
   double dt;
   int64_t n_steps;
-  const double* q0;     // initial state (r), for metrics runs: Qhat column 0
-  // metrics (optional)
-  const double* Qhat;   // reference data r_max x k (ld ldqh) for the training error
+  const double* q0;     // initial state (first r entries)
+  // metrics (metrics = 1): training error over the first k states against Qhat (ld ldqh)
+  int metrics;
+  const double* Qhat;
   int64_t ldqh, k;
-  const double* mu;     // temporal mean of the reference (r)
-  const double* denom;  // max_{t<k,i} |qhat - mu|
   double max_growth;
-  double* train_err;    // per candidate (indexed by cand0 + blockIdx.x)
+  double* train_err;
   double* growth;
   int* status;
-  int cand0;
-  // trajectory output (optional): n_steps x r row-major; rows after the first non-finite
+  // trajectory output (traj = 1): n_steps x r row-major; rows after the first non-finite
   // state are not written
-  double* traj;
+  int traj;
+  double* traj_out;
   int* finite;
 };
 
-int launch_rollouts(const RolloutArgs& a, int n_cand, bool metrics, bool traj, cudaStream_t st);
+size_t rollout_smem_bytes(int cluster, int r_max, int d_max);
+// Cluster size in {1, 2, 4, 8}, at least `want`, with the operator slice in shared memory; 0 if none fits.
+int rollout_cluster_size(int r_max, int d_max, int want);
+int launch_rollouts(RolloutBatch bt, int cluster, cudaStream_t st);
+int learn_set_cluster(int c);
 
 }  // namespace dopinf

@@ -16,13 +16,17 @@ namespace dopinf {
 namespace {
 
 constexpr int TM = 64, TN = 64, BK = 16, NT = 256;
-constexpr int kTargetCtas = 152 * 4;
+// Resident CTAs on GB300: 152 SMs x 3 (the register limit of this kernel).  The plan targets
+// this count independently of the device queried, so results do not depend on the device.
+constexpr int kSlots = 152 * 3;
 
 struct TnPlan {
-  int tiles_m, tiles_n, ntiles, splits;
+  int tiles_m, tiles_n, ntiles, splits, units, grid;
   int64_t rows_per_split;
 };
 
+// Units = (tile, row split) pairs; a persistent grid walks them.  The split count is chosen so
+// that the units fill whole waves of the resident slots (every unit costs the same).
 TnPlan make_plan(int64_t K, int64_t M, int64_t N, int sym) {
   TnPlan p;
   p.tiles_m = (int)((M + TM - 1) / TM);
@@ -31,15 +35,26 @@ TnPlan make_plan(int64_t K, int64_t M, int64_t N, int sym) {
   if (p.ntiles < 1) p.ntiles = 1;
   int64_t max_splits = (K + BK * 8 - 1) / (BK * 8);  // at least 128 rows per split
   if (max_splits < 1) max_splits = 1;
-  int64_t splits = (kTargetCtas + p.ntiles - 1) / p.ntiles;
-  if (splits > max_splits) splits = max_splits;
-  if (splits < 1) splits = 1;
-  int64_t rps = (K + splits - 1) / splits;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int sp = 1; sp <= 4 * kSlots && sp <= max_splits; ++sp) {
+    const int64_t units = (int64_t)p.ntiles * sp;
+    const int64_t waves = (units + kSlots - 1) / kSlots;
+    const double eff = (double)units / (double)(waves * kSlots) - 0.0005 * sp;
+    if (eff > best_eff) {
+      best_eff = eff;
+      best = sp;
+    }
+    if (units >= 8 * kSlots) break;
+  }
+  int64_t rps = (K + best - 1) / best;
   rps = (rps + BK - 1) / BK * BK;
   if (rps < BK) rps = BK;
   p.rows_per_split = rps;
   p.splits = (int)((K + rps - 1) / rps);
   if (p.splits < 1) p.splits = 1;
+  p.units = p.ntiles * p.splits;
+  p.grid = p.units < kSlots ? p.units : kSlots;
   return p;
 }
 
@@ -63,14 +78,16 @@ template <typename T>
 __global__ void __launch_bounds__(NT) tn_partial(const T* __restrict__ A, int64_t lda,
                                                  const T* __restrict__ B, int64_t ldb, int64_t K,
                                                  int64_t M, int64_t N, int64_t rows_per_split,
-                                                 int tiles_m, int tiles_n, int sym, int ntiles,
+                                                 int tiles_m, int tiles_n, int sym, int ntiles, int units,
                                                  double* __restrict__ part) {
   __shared__ double As[BK][TM + 1];
   __shared__ double Bs[BK][TN + 1];
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+  const int tile = u % ntiles, split = u / ntiles;
   int bi, bj;
-  tile_coords(blockIdx.x, tiles_m, tiles_n, sym, bi, bj);
+  tile_coords(tile, tiles_m, tiles_n, sym, bi, bj);
   const int64_t m0 = (int64_t)bi * TM, n0 = (int64_t)bj * TN;
-  const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t k0 = (int64_t)split * rows_per_split;
   const int64_t k1 = k0 + rows_per_split < K ? k0 + rows_per_split : K;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -106,11 +123,12 @@ __global__ void __launch_bounds__(NT) tn_partial(const T* __restrict__ A, int64_
     }
     __syncthreads();
   }
-  double* out = part + ((size_t)blockIdx.y * ntiles + blockIdx.x) * (TM * TN);
+  double* out = part + (size_t)u * (TM * TN);  // u = split * ntiles + tile
 #pragma unroll
   for (int j = 0; j < 4; ++j)
 #pragma unroll
     for (int i = 0; i < 4; ++i) out[(ty + 16 * j) * TM + tx + 16 * i] = acc[i][j];
+  }
 }
 
 __global__ void __launch_bounds__(NT) tn_reduce(const double* __restrict__ part, int splits, int ntiles,
@@ -148,15 +166,14 @@ int tn_product(const void* A, int64_t lda, const void* B, int64_t ldb, int dtype
   if (!ws || ws_bytes < tn_workspace(K, M, N, sym) || misaligned(ws)) return DOPINF_E_ARG;
   Carver cv(ws);
   double* part = cv.take<double>((size_t)p.splits * p.ntiles * TM * TN);
-  dim3 grid(p.ntiles, p.splits);
   if (dtype == DOPINF_F64)
-    tn_partial<double><<<grid, NT, 0, st>>>(static_cast<const double*>(A), lda, static_cast<const double*>(B),
-                                            ldb, K, M, N, p.rows_per_split, p.tiles_m, p.tiles_n, sym,
-                                            p.ntiles, part);
+    tn_partial<double><<<p.grid, NT, 0, st>>>(static_cast<const double*>(A), lda, static_cast<const double*>(B),
+                                              ldb, K, M, N, p.rows_per_split, p.tiles_m, p.tiles_n, sym,
+                                              p.ntiles, p.units, part);
   else if (dtype == DOPINF_F32)
-    tn_partial<float><<<grid, NT, 0, st>>>(static_cast<const float*>(A), lda, static_cast<const float*>(B),
-                                           ldb, K, M, N, p.rows_per_split, p.tiles_m, p.tiles_n, sym,
-                                           p.ntiles, part);
+    tn_partial<float><<<p.grid, NT, 0, st>>>(static_cast<const float*>(A), lda, static_cast<const float*>(B),
+                                             ldb, K, M, N, p.rows_per_split, p.tiles_m, p.tiles_n, sym,
+                                             p.ntiles, p.units, part);
   else
     return DOPINF_E_ARG;
   DOPINF_TRY(launch_status());
@@ -171,6 +188,8 @@ using namespace dopinf;
 
 DOPINF_API size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode) {
   (void)dtype;
+  if (n < 0 || k < 1) return 0;
+  if (mode == DOPINF_GRAM_BF16X4) return gram_tc_workspace(n, k);
   if (mode != DOPINF_GRAM_FP64) return 0;
   return tn_workspace(n, k, k, 1);
 }
@@ -180,11 +199,12 @@ DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64
                            void* stream) {
   if (n < 0 || k < 1 || ldq < (n > 1 ? n : 1) || ldd < k || !D || (n > 0 && !Q)) return DOPINF_E_ARG;
   if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
-  if (mode != DOPINF_GRAM_FP64) return DOPINF_E_UNSUPPORTED;
+  if (mode != DOPINF_GRAM_FP64 && mode != DOPINF_GRAM_BF16X4) return DOPINF_E_UNSUPPORTED;
   if (n == 0) {
     if (accumulate) return DOPINF_OK;
     return cuda_status(cudaMemset2DAsync(D, ldd * sizeof(double), 0, k * sizeof(double), k,
                                          as_stream(stream)));
   }
+  if (mode == DOPINF_GRAM_BF16X4) return gram_tc(Q, dtype, n, k, ldq, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
   return tn_product(Q, ldq, Q, ldq, dtype, n, k, k, 1, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
 }

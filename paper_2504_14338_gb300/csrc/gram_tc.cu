@@ -1,0 +1,450 @@
+// Split-precision method-of-snapshots Gram D = Q^T Q (Section 3.4, eq. mos_partitioned) on
+// the tcgen05 tensor cores.
+//
+// Each value is split into two BF16 slices, x = h + l + e with h = bf16(x) and
+// l = bf16(x - h) (x - h is exact in the source precision), |e| <= 2^-17 |x|.  Then
+// Q^T Q ~= H^T H + H^T L + L^T H + L^T L: four BF16 products per 128 x 128 output tile.  The
+// terms left out (those with e) change sign from row to row and grow like sqrt(n) against
+// the n-fold sum.
+//
+// Accumulation.  The tensor core's FP32 accumulation rounds toward zero by about half an ulp
+// per MMA (measured on GB300: the diagonal of a long sum drifts low in proportion to the number
+// of MMAs).  So the MMA accumulator is restarted for every drain chunk (default: one stage of
+// 64 rows), the three small slice products of a stage are issued before the large H^T H one
+// (only 4 MMAs then add to a large accumulator), and each chunk sum is added to an FP32
+// (hi, lo) pair kept in tensor memory with Knuth's TwoSum, which carries the running sum to
+// about 2^-44.  At the end of a work unit (tile, row range) hi + lo is written in FP64; a final
+// kernel adds the units of a tile in a fixed order and mirrors the upper triangle, so D is
+// exactly symmetric and reproducible run to run.
+//
+// Kernel structure (one persistent CTA per SM, 320 threads):
+//   warp 0    TMA producer: H and L tiles of the a-block and of the b-block (128 snapshots x
+//             64 rows each, 128-byte swizzle) into a 3-stage shared ring;
+//   warp 1    TMEM allocator and single-thread MMA issuer: tcgen05.mma M = 128, N = 128,
+//             K = 16 into one of two TMEM accumulators;
+//   warps 2-9 drain: tcgen05.ld of the finished accumulator, TwoSum into (hi, lo) in TMEM.
+// TMEM columns: [0, 128) and [128, 256) accumulators, [256, 384) hi, [384, 512) lo.
+// Work units are ordered split-major, so the CTAs running together read the same rows and
+// the slices come from HBM about once.  Every mbarrier wait is bounded in time; on expiry the
+// kernel records an error, lets its copies and MMAs finish (again with bounded waits), frees
+// TMEM and returns.
+#include "common.cuh"
+#include "sm100.cuh"
+#include <cuda_bf16.h>
+
+namespace dopinf {
+namespace {
+
+using namespace sm100;
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int STAGES = 3;
+constexpr uint32_t TILE = BM * BK * 2;         // 16 KB: one slice of one block
+constexpr uint32_t STAGE_BYTES = 4 * TILE;     // Ah, Al, Bh, Bl
+constexpr size_t SMEM_BYTES = STAGES * (size_t)STAGE_BYTES + 1024;
+constexpr int NDRAIN = 8;
+constexpr int NTHREADS = 64 + 32 * NDRAIN;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_HI = 256, COL_LO = 384;
+int64_t g_chunk_rows = 64;  // rows summed by one MMA accumulator before the TwoSum drain (tunable)
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr int kSmTarget = 152;  // the work split targets GB300's SM count, independent of the device queried
+
+struct TcShape {
+  int64_t n;
+  int k, tn, ntiles, splits, units;
+  int64_t rows_per_split, chunk_rows;
+};
+
+// upper-triangle tiles (ta <= tb) of a tn x tn tile grid, row-major
+__host__ __device__ inline void tile_of(int t, int tn, int& ta, int& tb) {
+  ta = 0;
+  while (t >= tn - ta) {
+    t -= tn - ta;
+    ++ta;
+  }
+  tb = ta + t;
+}
+__host__ __device__ inline int tile_index(int ta, int tb, int tn) { return ta * tn - ta * (ta - 1) / 2 + (tb - ta); }
+
+__device__ __forceinline__ float two_sum_hi(float hi, float a, float& err) {
+  const float s = __fadd_rn(hi, a);
+  const float z = __fsub_rn(s, hi);
+  err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(a, z));
+  return s;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    gram_bf16x4_kernel(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapL, TcShape sh,
+                       double* __restrict__ part, unsigned* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], drain_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], NDRAIN);
+    }
+    mbar_init(&drain_bar, 1);
+    abort_sh = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&mapH);
+    tma_prefetch_desc(&mapL);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base_sh, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  auto fail = [&](unsigned code) {
+    atomicOr(err, code);
+    abort_sh = 1;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- TMA producer
+      int stage = 0;
+      int64_t it = 0;
+      for (int u = blockIdx.x; u < sh.units && !abort_sh; u += gridDim.x) {
+        int ta, tb;
+        tile_of(u % sh.ntiles, sh.tn, ta, tb);
+        const int64_t k0 = (int64_t)(u / sh.ntiles) * sh.rows_per_split;
+        const int64_t k1 = k0 + sh.rows_per_split < sh.n ? k0 + sh.rows_per_split : sh.n;
+        for (int64_t row = k0; row < k1 && !abort_sh; row += BK) {
+          if (it >= STAGES && !mbar_wait(&empty_bar[stage], (uint32_t)((it / STAGES) - 1) & 1u, kWaitNs)) {
+            fail(1u);
+            break;
+          }
+          uint8_t* base = smem + (size_t)stage * STAGE_BYTES;
+          mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
+          const int x = (int)row;
+          tma_load_2d(base, &mapH, &full_bar[stage], x, ta * BM);
+          tma_load_2d(base + TILE, &mapL, &full_bar[stage], x, ta * BM);
+          tma_load_2d(base + 2 * TILE, &mapH, &full_bar[stage], x, tb * BN);
+          tma_load_2d(base + 3 * TILE, &mapL, &full_bar[stage], x, tb * BN);
+          stage = (stage + 1) % STAGES;
+          ++it;
+        }
+      }
+      // let the last copies land before the CTA can exit (bounded)
+      for (int64_t j = it - STAGES > 0 ? it - STAGES : 0; j < it; ++j)
+        mbar_wait(&full_bar[j % STAGES], (uint32_t)(j / STAGES) & 1u, kWaitNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA issuer
+      const uint32_t idesc = idesc_bf16_f32(BM, BN);
+      int stage = 0;
+      int64_t it = 0, chunk = 0;
+      bool issued = false;
+      for (int u = blockIdx.x; u < sh.units && !abort_sh; u += gridDim.x) {
+        const int64_t k0 = (int64_t)(u / sh.ntiles) * sh.rows_per_split;
+        const int64_t k1 = k0 + sh.rows_per_split < sh.n ? k0 + sh.rows_per_split : sh.n;
+        for (int64_t c0 = k0; c0 < k1 && !abort_sh; c0 += sh.chunk_rows) {
+          const int buf = (int)(chunk & 1);
+          if (chunk >= 2 && !mbar_wait(&acce_bar[buf], (uint32_t)((chunk >> 1) - 1) & 1u, kWaitNs)) {
+            fail(2u);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dacc = tmem + (uint32_t)(buf * BN);
+          const int64_t c1 = c0 + sh.chunk_rows < k1 ? c0 + sh.chunk_rows : k1;
+          bool first = true;
+          for (int64_t row = c0; row < c1; row += BK) {
+            if (!mbar_wait(&full_bar[stage], (uint32_t)(it / STAGES) & 1u, kWaitNs)) {
+              fail(4u);
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE_BYTES);
+            const uint32_t ah = sa, al = sa + TILE, bh = sa + 2 * TILE, bl = sa + 3 * TILE;
+            // the three small slice products first, then H^T H: only 4 MMAs add to a large sum
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t o = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzled row
+              mma_bf16(dacc, sdesc_k_sw128(al + o), sdesc_k_sw128(bl + o), idesc, first && kk == 0 ? 0u : 1u);
+              mma_bf16(dacc, sdesc_k_sw128(ah + o), sdesc_k_sw128(bl + o), idesc, 1u);
+              mma_bf16(dacc, sdesc_k_sw128(al + o), sdesc_k_sw128(bh + o), idesc, 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t o = kk * 32;
+              mma_bf16(dacc, sdesc_k_sw128(ah + o), sdesc_k_sw128(bh + o), idesc, 1u);
+            }
+            issued = true;
+            first = false;
+            mma_commit(&empty_bar[stage]);
+            stage = (stage + 1) % STAGES;
+            ++it;
+          }
+          if (abort_sh) break;
+          mma_commit(&accf_bar[buf]);
+          ++chunk;
+        }
+      }
+      if (issued) {  // every MMA of this thread complete before TMEM is released
+        mma_commit(&drain_bar);
+        mbar_wait(&drain_bar, 0u, kWaitNs);
+      }
+    }
+  } else {
+    // --------------------------------------------------------------- drain (warps 2-9)
+    const int q = warp & 3;               // TMEM lane quadrant this warp may access
+    const int c0w = ((warp - 2) >> 2) * 64;  // this warp's 64 columns
+    const int row = q * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    int64_t chunk = 0;
+    for (int u = blockIdx.x; u < sh.units && !abort_sh; u += gridDim.x) {
+      const int64_t k0 = (int64_t)(u / sh.ntiles) * sh.rows_per_split;
+      const int64_t k1 = k0 + sh.rows_per_split < sh.n ? k0 + sh.rows_per_split : sh.n;
+      bool ok = true;
+      for (int64_t c0 = k0; c0 < k1; c0 += sh.chunk_rows) {
+        const int buf = (int)(chunk & 1);
+        ok = mbar_wait(&accf_bar[buf], (uint32_t)(chunk >> 1) & 1u, kWaitNs);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          if (lane == 0) fail(8u);
+          break;
+        }
+        tc_fence_after();
+        const bool first = c0 == k0;
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+          const uint32_t col = (uint32_t)(c0w + g * 32);
+          uint32_t a[32], hi[32], lo[32];
+          tmem_ld_32x32b_x32(tmem + lane_off + (uint32_t)(buf * BN) + col, a);
+          if (!first) {
+            tmem_ld_32x32b_x32(tmem + lane_off + COL_HI + col, hi);
+            tmem_ld_32x32b_x32(tmem + lane_off + COL_LO + col, lo);
+          }
+          tmem_wait_ld();
+          if (first) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              hi[j] = a[j];
+              lo[j] = 0u;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float e;
+              const float s = two_sum_hi(__uint_as_float(hi[j]), __uint_as_float(a[j]), e);
+              hi[j] = __float_as_uint(s);
+              lo[j] = __float_as_uint(__fadd_rn(__uint_as_float(lo[j]), e));
+            }
+          }
+          tmem_st_32x32b_x32(tmem + lane_off + COL_HI + col, hi);
+          tmem_st_32x32b_x32(tmem + lane_off + COL_LO + col, lo);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[buf]);
+        ++chunk;
+      }
+      if (!ok) break;
+      // unit finished: hi + lo of this warp's columns, in FP64, to the unit's partial tile
+      double* P = part + (size_t)u * BM * BN;
+#pragma unroll 1
+      for (int g = 0; g < 2; ++g) {
+        const uint32_t col = (uint32_t)(c0w + g * 32);
+        uint32_t hi[32], lo[32];
+        tmem_ld_32x32b_x32(tmem + lane_off + COL_HI + col, hi);
+        tmem_ld_32x32b_x32(tmem + lane_off + COL_LO + col, lo);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          P[(size_t)(col + j) * BM + row] = (double)__uint_as_float(hi[j]) + (double)__uint_as_float(lo[j]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// D[a, b] = D[b, a] = sum over the row splits (in order) of the unit partials, a <= b.
+__global__ void gram_tc_reduce(const double* __restrict__ part, TcShape sh, int accumulate, double* __restrict__ D,
+                               int64_t ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t kk = sh.k;
+  if (e >= kk * kk) return;
+  const int a = (int)(e % kk), b = (int)(e / kk);
+  if (a > b) return;
+  const int ta = a / BM, tb = b / BN;
+  const int t = tile_index(ta, tb, sh.tn);
+  const size_t off = (size_t)(b - tb * BN) * BM + (a - ta * BM);
+  double s = 0.0;
+  for (int sp = 0; sp < sh.splits; ++sp) s += part[((size_t)sp * sh.ntiles + t) * BM * BN + off];
+  if (accumulate) s += D[a + (int64_t)b * ldd];
+  D[a + (int64_t)b * ldd] = s;
+  D[b + (int64_t)a * ldd] = s;
+}
+
+// h = bf16(x), l = bf16(x - h), planes with leading dimension lds.
+template <typename T>
+__global__ void split_bf16(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq, __nv_bfloat16* __restrict__ H,
+                           __nv_bfloat16* __restrict__ L, int64_t lds) {
+  const int64_t total = n * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, t = e / n;
+    const T x = Q[i + t * ldq];
+    __nv_bfloat16 h, l;
+    if constexpr (sizeof(T) == 8) {
+      h = __double2bfloat16(x);
+      l = __double2bfloat16(x - (double)__bfloat162float(h));
+    } else {
+      h = __float2bfloat16_rn(x);
+      l = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+    H[i + t * lds] = h;
+    L[i + t * lds] = l;
+  }
+}
+
+TcShape make_shape(int64_t n, int64_t k) {
+  const int sms = kSmTarget;
+  TcShape s;
+  s.n = n;
+  s.k = (int)k;
+  s.tn = (int)((k + BM - 1) / BM);
+  s.ntiles = s.tn * (s.tn + 1) / 2;
+  // choose the row split so that the units fill whole waves of SMs as evenly as possible
+  const int64_t max_split = (n + 4 * BK - 1) / (4 * BK) > 0 ? (n + 4 * BK - 1) / (4 * BK) : 1;
+  int best = 1;
+  double best_eff = -1.0;
+  for (int sp = 1; sp <= 256 && sp <= max_split; ++sp) {
+    const int64_t units = (int64_t)s.ntiles * sp;
+    const int64_t waves = (units + sms - 1) / sms;
+    const double eff = (double)units / (double)(waves * sms) - 0.0005 * sp;  // prefer fewer splits on ties
+    if (eff > best_eff) {
+      best_eff = eff;
+      best = sp;
+    }
+    if (units >= 16 * sms) break;
+  }
+  int64_t rps = (n + best - 1) / best;
+  rps = (rps + BK - 1) / BK * BK;
+  s.rows_per_split = rps;
+  s.splits = (int)((n + rps - 1) / rps);
+  if (s.splits < 1) s.splits = 1;
+  s.units = s.ntiles * s.splits;
+  s.chunk_rows = rps < g_chunk_rows ? rps : g_chunk_rows;
+  return s;
+}
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D map over a BF16 plane (inner dimension n rows, outer k columns, leading dimension
+// lds elements), box of 64 rows x 128 columns, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* map, void* base, int64_t n, int64_t k, int64_t lds) {
+  EncodeTiledFn f = encode_fn();
+  if (!f) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
+  cuuint64_t strides[1] = {(cuuint64_t)(lds * 2)};
+  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t estr[2] = {1, 1};
+  return f(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcWs {
+  __nv_bfloat16 *H, *L;
+  double* part;
+  unsigned* err;
+  int64_t lds;
+  size_t used;
+};
+
+TcWs carve_tc(void* base, int64_t n, int64_t k) {
+  const TcShape s = make_shape(n, k);
+  Carver c(base);
+  TcWs w;
+  w.lds = (n + 63) / 64 * 64;
+  w.H = c.take<__nv_bfloat16>((size_t)w.lds * k);
+  w.L = c.take<__nv_bfloat16>((size_t)w.lds * k);
+  w.part = c.take<double>((size_t)s.units * BM * BN);
+  w.err = c.take<unsigned>(1);
+  w.used = c.used;
+  return w;
+}
+
+}  // namespace
+
+size_t gram_tc_workspace(int64_t n, int64_t k) { return carve_tc(nullptr, n, k).used; }
+
+int64_t gram_tc_set_chunk_rows(int64_t rows) {
+  const int64_t prev = g_chunk_rows;
+  if (rows > 0) g_chunk_rows = (rows + BK - 1) / BK * BK;
+  return prev;
+}
+
+int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
+            void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (n > ((int64_t)1 << 31) - BK || k > 65535) return DOPINF_E_UNSUPPORTED;
+  if (!ws || ws_bytes < gram_tc_workspace(n, k) || misaligned(ws)) return DOPINF_E_ARG;
+  TcWs w = carve_tc(ws, n, k);
+  const TcShape sh = make_shape(n, k);
+  const int64_t total = n * k;
+  const unsigned sblocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+  if (dtype == DOPINF_F64)
+    split_bf16<double><<<sblocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.H, w.L, w.lds);
+  else
+    split_bf16<float><<<sblocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.H, w.L, w.lds);
+  DOPINF_TRY(launch_status());
+  CUtensorMap mh, ml;
+  if (!make_map(&mh, w.H, n, k, w.lds) || !make_map(&ml, w.L, n, k, w.lds)) return DOPINF_E_CUDA;
+  DOPINF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(unsigned), st));
+  DOPINF_CUDA(cudaFuncSetAttribute(gram_bf16x4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  const int grid = sh.units < num_sms() ? sh.units : num_sms();
+  gram_bf16x4_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(mh, ml, sh, w.part, w.err);
+  DOPINF_TRY(launch_status());
+  const int64_t kk = k * k;
+  gram_tc_reduce<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(w.part, sh, accumulate, D, ldd);
+  DOPINF_TRY(launch_status());
+  unsigned e = 0;
+  DOPINF_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  DOPINF_CUDA(cudaStreamSynchronize(st));
+  return e ? DOPINF_E_TIMEOUT : DOPINF_OK;
+}
+
+}  // namespace dopinf

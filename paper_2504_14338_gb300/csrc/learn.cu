@@ -80,27 +80,33 @@ __global__ void __launch_bounds__(LB) train_stats(const double* __restrict__ Qha
   }
 }
 
-// One CTA per regularisation pair of one r.  M (d x d) and X (d x r) live in the workspace
-// (L2-resident for the sizes of Step IV).  Right-looking Cholesky M = L L^T, then
+// One CTA per candidate (every r and pair in one launch).  M (d x d) and X (d x r) live in
+// the workspace (L2-resident for the sizes of Step IV).  Right-looking Cholesky M = L L^T, then
 // L Z = B, L^T X = Z.  A non-positive or non-finite pivot marks the candidate (status 1).
-__global__ void __launch_bounds__(CB) chol_solve(const double* __restrict__ G, const double* __restrict__ B, int r,
-                                                 int d, const double* __restrict__ beta1, const double* __restrict__ beta2,
-                                                 int n_b2, double* __restrict__ Mws, double* __restrict__ Xws,
-                                                 double* __restrict__ Oall, int* __restrict__ status, int cand0) {
+struct CholCand {
+  const double* G;  // d x d normal matrix of this candidate's r
+  const double* B;  // d x r right-hand sides
+  double* M;        // d x d scratch (factorised in place)
+  double* X;        // d x r solution
+  double* O;        // r x d operator output (ld r)
+  double b1, b2;
+  int r, d, cand;
+};
+
+__global__ void __launch_bounds__(CB) chol_solve(const CholCand* __restrict__ table, int* __restrict__ status) {
   __shared__ int s_fail;
-  const int p = blockIdx.x;
-  const double b1 = beta1[p / n_b2], b2 = beta2[p % n_b2];
-  const int s = d - r - 1;
-  double* M = Mws + (size_t)p * d * d;
-  double* X = Xws + (size_t)p * d * r;
+  const CholCand cc = table[blockIdx.x];
+  const int r = cc.r, d = cc.d, s = d - r - 1;
+  double* M = cc.M;
+  double* X = cc.X;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = CB / 32;
   for (int64_t e = tid; e < (int64_t)d * d; e += CB) {
     const int i = (int)(e % d), c = (int)(e / d);
-    double v = G[e];
-    if (i == c) v += (i < r || i == r + s) ? b1 : b2;
+    double v = cc.G[e];
+    if (i == c) v += (i < r || i == r + s) ? cc.b1 : cc.b2;
     M[e] = v;
   }
-  for (int64_t e = tid; e < (int64_t)d * r; e += CB) X[e] = B[e];
+  for (int64_t e = tid; e < (int64_t)d * r; e += CB) X[e] = cc.B[e];
   if (tid == 0) s_fail = 0;
   __syncthreads();
   for (int j = 0; j < d; ++j) {
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(CB) chol_solve(const double* __restrict__ G, c
   }
   __syncthreads();
   if (s_fail) {
-    if (tid == 0) status[cand0 + p] = 1;
+    if (tid == 0) status[cc.cand] = 1;
     return;
   }
   // forward: L Z = B (column j of L scales row j, then updates the rows below)
@@ -149,12 +155,11 @@ __global__ void __launch_bounds__(CB) chol_solve(const double* __restrict__ G, c
     }
     __syncthreads();
   }
-  double* O = Oall + (size_t)p * r * d;  // r x d, ld r
   for (int64_t e = tid; e < (int64_t)r * d; e += CB) {
     const int i = (int)(e % r), a = (int)(e / r);
-    O[e] = X[a + (size_t)i * d];
+    cc.O[e] = X[a + (size_t)i * d];
   }
-  if (tid == 0) status[cand0 + p] = 0;
+  if (tid == 0) status[cc.cand] = 0;
 }
 
 __global__ void select_best(const double* err, const int* status, int n_cand, int* best) {
@@ -165,40 +170,45 @@ __global__ void select_best(const double* err, const int* status, int n_cand, in
   *best = b;
 }
 
+inline int dim_d(int r) { return r + r * (r + 1) / 2 + 1; }
+
+constexpr int kMaxR = 64;  // entries of the r list
+
+// Workspace layout, one for the size query (base == nullptr) and for the entry point.
 struct LearnWs {
-  double *beta1, *beta2, *Oall, *mu, *denom, *Dh, *Y, *G, *B, *M, *X;
+  CholCand* chol;
+  RolloutCand* roll;
+  double *mu, *denom, *Dh, *Y;
+  double *G[kMaxR], *B[kMaxR], *M[kMaxR], *X[kMaxR], *O[kMaxR];
   int* best;
   void* tn;
   size_t tn_bytes, used;
-  size_t o_off[64];
 };
 
-inline int dim_d(int r) { return r + r * (r + 1) / 2 + 1; }
-
-LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1, int n_b2) {
+LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_pairs) {
   Carver c(base);
   LearnWs w;
   int d_max = 0, r_max = 0;
-  size_t o_total = 0;
   for (int i = 0; i < n_r; ++i) {
-    w.o_off[i] = o_total;
-    o_total += (size_t)n_b1 * n_b2 * r_list[i] * dim_d(r_list[i]);
     if (dim_d(r_list[i]) > d_max) d_max = dim_d(r_list[i]);
     if (r_list[i] > r_max) r_max = r_list[i];
   }
-  const int n_pairs = n_b1 * n_b2;
-  w.beta1 = c.take<double>(n_b1);
-  w.beta2 = c.take<double>(n_b2);
-  w.Oall = c.take<double>(o_total);
-  w.mu = c.take<double>(r_max);
-  w.denom = c.take<double>(1);
+  const int n_cand = n_r * n_pairs;
+  w.chol = c.take<CholCand>(n_cand);
+  w.roll = c.take<RolloutCand>(n_cand);
+  w.mu = c.take<double>((size_t)n_r * r_max);
+  w.denom = c.take<double>(n_r);
   w.best = c.take<int>(1);
   w.Dh = c.take<double>((size_t)K * d_max);
   w.Y = c.take<double>((size_t)K * r_max);
-  w.G = c.take<double>((size_t)d_max * d_max);
-  w.B = c.take<double>((size_t)d_max * r_max);
-  w.M = c.take<double>((size_t)n_pairs * d_max * d_max);
-  w.X = c.take<double>((size_t)n_pairs * d_max * r_max);
+  for (int i = 0; i < n_r; ++i) {
+    const size_t r = r_list[i], d = dim_d(r_list[i]);
+    w.G[i] = c.take<double>(d * d);
+    w.B[i] = c.take<double>(d * r);
+    w.M[i] = c.take<double>((size_t)n_pairs * d * d);
+    w.X[i] = c.take<double>((size_t)n_pairs * d * r);
+    w.O[i] = c.take<double>((size_t)n_pairs * r * d);
+  }
   size_t tb = 0;
   for (int i = 0; i < n_r; ++i) {
     const int r = r_list[i], d = dim_d(r);
@@ -212,7 +222,16 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1,
   return w;
 }
 
+int g_cluster_want = 4;  // tunable: preferred CTAs per candidate in the rollouts
+
 }  // namespace
+
+int learn_set_cluster(int c) {
+  const int prev = g_cluster_want;
+  if (c == 1 || c == 2 || c == 4 || c == 8) g_cluster_want = c;
+  return prev;
+}
+
 }  // namespace dopinf
 
 using namespace dopinf;
@@ -221,35 +240,72 @@ static int64_t learn_rows(int64_t k, int mode) { return mode == DOPINF_DISCRETE 
 
 DOPINF_API size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1, int n_b2) {
   (void)r_max;
-  if (!r_list || n_r < 1 || n_r > 64 || n_b1 < 1 || n_b2 < 1 || k < 3) return 0;
-  return carve_learn(nullptr, k - 1, r_list, n_r, n_b1, n_b2).used;
+  if (!r_list || n_r < 1 || n_r > kMaxR || n_b1 < 1 || n_b2 < 1 || k < 3) return 0;
+  return carve_learn(nullptr, k - 1, r_list, n_r, n_b1 * n_b2).used;
 }
 
 DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
                             const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt,
                             int64_t n_steps, double max_growth, double* train_err, double* growth, int* cand_status,
                             int* best_out, double* O_best, void* ws, size_t ws_bytes, void* stream) {
-  if (!Qhat || r_max < 1 || ldqh < r_max || !r_list || n_r < 1 || n_r > 64 || !beta1 || !beta2 || n_b1 < 1 ||
+  if (!Qhat || r_max < 1 || ldqh < r_max || !r_list || n_r < 1 || n_r > kMaxR || !beta1 || !beta2 || n_b1 < 1 ||
       n_b2 < 1 || !train_err || !growth || !cand_status || !best_out || !O_best)
     return DOPINF_E_ARG;
   if (mode != DOPINF_DISCRETE && mode != DOPINF_CONTINUOUS_RK4) return DOPINF_E_ARG;
   if (mode == DOPINF_CONTINUOUS_RK4 && !(dt > 0.0)) return DOPINF_E_ARG;
   const int64_t K = learn_rows(k, mode);
   if (K < 1 || n_steps < k || !(max_growth > 0.0)) return DOPINF_E_ARG;
-  for (int i = 0; i < n_r; ++i)
+  int d_max = 0, r_used = 0;
+  for (int i = 0; i < n_r; ++i) {
     if (r_list[i] < 1 || r_list[i] > r_max || r_list[i] > 255) return DOPINF_E_ARG;
+    d_max = dim_d(r_list[i]) > d_max ? dim_d(r_list[i]) : d_max;
+    r_used = r_list[i] > r_used ? r_list[i] : r_used;
+  }
   for (int i = 0; i < n_b1; ++i)
     if (!(beta1[i] >= 0.0)) return DOPINF_E_ARG;
   for (int i = 0; i < n_b2; ++i)
     if (!(beta2[i] >= 0.0)) return DOPINF_E_ARG;
   if (!ws || ws_bytes < dopinf_learn_workspace(r_max, k, r_list, n_r, n_b1, n_b2) || misaligned(ws))
     return DOPINF_E_ARG;
+  const int cluster = rollout_cluster_size(r_used, d_max, r_used >= 16 ? g_cluster_want : 1);
+  if (!cluster) return DOPINF_E_UNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   // the workspace is laid out for K = k - 1 rows, which covers both modes
-  LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1, n_b2);
+  LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1 * n_b2);
   const int n_pairs = n_b1 * n_b2, n_cand = n_r * n_pairs;
-  DOPINF_CUDA(cudaMemcpyAsync(w.beta1, beta1, sizeof(double) * n_b1, cudaMemcpyHostToDevice, st));
-  DOPINF_CUDA(cudaMemcpyAsync(w.beta2, beta2, sizeof(double) * n_b2, cudaMemcpyHostToDevice, st));
+  // candidate tables, built on the host: c = (ir * n_b1 + i1) * n_b2 + i2
+  CholCand* ch = new CholCand[n_cand];
+  RolloutCand* ro = new RolloutCand[n_cand];
+  for (int ir = 0; ir < n_r; ++ir) {
+    const int r = r_list[ir], d = dim_d(r);
+    for (int p = 0; p < n_pairs; ++p) {
+      const int c = ir * n_pairs + p;
+      ch[c].G = w.G[ir];
+      ch[c].B = w.B[ir];
+      ch[c].M = w.M[ir] + (size_t)p * d * d;
+      ch[c].X = w.X[ir] + (size_t)p * d * r;
+      ch[c].O = w.O[ir] + (size_t)p * r * d;
+      ch[c].b1 = beta1[p / n_b2];
+      ch[c].b2 = beta2[p % n_b2];
+      ch[c].r = r;
+      ch[c].d = d;
+      ch[c].cand = c;
+      ro[c].O = ch[c].O;
+      ro[c].ldo = r;
+      ro[c].r = r;
+      ro[c].d = d;
+      ro[c].cand = c;
+      ro[c].mu = w.mu + (size_t)ir * r_max;
+      ro[c].denom = w.denom + ir;
+    }
+  }
+  // pageable host -> device copies: the runtime stages the source before returning
+  cudaError_t e1 = cudaMemcpyAsync(w.chol, ch, sizeof(CholCand) * n_cand, cudaMemcpyHostToDevice, st);
+  cudaError_t e2 = cudaMemcpyAsync(w.roll, ro, sizeof(RolloutCand) * n_cand, cudaMemcpyHostToDevice, st);
+  delete[] ch;
+  delete[] ro;
+  DOPINF_CUDA(e1);
+  DOPINF_CUDA(e2);
   const int64_t t0 = mode == DOPINF_DISCRETE ? 0 : 1;
   for (int ir = 0; ir < n_r; ++ir) {
     const int r = r_list[ir], d = dim_d(r);
@@ -257,34 +313,31 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     const unsigned blocks = (unsigned)((tot + LB - 1) / LB < 4096 ? (tot + LB - 1) / LB : 4096);
     build_features<<<blocks, LB, 0, st>>>(Qhat, ldqh, r, d, K, t0, mode, dt, w.Dh, w.Y);
     DOPINF_TRY(launch_status());
-    DOPINF_TRY(tn_product(w.Dh, K, w.Dh, K, DOPINF_F64, K, d, d, 1, 0, w.G, d, w.tn, w.tn_bytes, st));
-    DOPINF_TRY(tn_product(w.Dh, K, w.Y, K, DOPINF_F64, K, d, r, 0, 0, w.B, d, w.tn, w.tn_bytes, st));
-    train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu, w.denom);
-    chol_solve<<<n_pairs, CB, 0, st>>>(w.G, w.B, r, d, w.beta1, w.beta2, n_b2, w.M, w.X, w.Oall + w.o_off[ir],
-                                        cand_status, ir * n_pairs);
+    DOPINF_TRY(tn_product(w.Dh, K, w.Dh, K, DOPINF_F64, K, d, d, 1, 0, w.G[ir], d, w.tn, w.tn_bytes, st));
+    DOPINF_TRY(tn_product(w.Dh, K, w.Y, K, DOPINF_F64, K, d, r, 0, 0, w.B[ir], d, w.tn, w.tn_bytes, st));
+    train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * r_max, w.denom + ir);
     DOPINF_TRY(launch_status());
-    RolloutArgs a = {};
-    a.O = w.Oall + w.o_off[ir];
-    a.o_stride = (int64_t)r * d;
-    a.ldo = r;
-    a.r = r;
-    a.d = d;
-    a.mode = mode;
-    a.dt = dt;
-    a.n_steps = n_steps;
-    a.q0 = Qhat;
-    a.Qhat = Qhat;
-    a.ldqh = ldqh;
-    a.k = k;
-    a.mu = w.mu;
-    a.denom = w.denom;
-    a.max_growth = max_growth;
-    a.train_err = train_err;
-    a.growth = growth;
-    a.status = cand_status;
-    a.cand0 = ir * n_pairs;
-    DOPINF_TRY(launch_rollouts(a, n_pairs, true, false, st));
   }
+  chol_solve<<<n_cand, CB, 0, st>>>(w.chol, cand_status);
+  DOPINF_TRY(launch_status());
+  RolloutBatch bt = {};
+  bt.cands = w.roll;
+  bt.n_cand = n_cand;
+  bt.r_max = r_used;
+  bt.d_max = d_max;
+  bt.mode = mode;
+  bt.dt = dt;
+  bt.n_steps = n_steps;
+  bt.q0 = Qhat;
+  bt.metrics = 1;
+  bt.Qhat = Qhat;
+  bt.ldqh = ldqh;
+  bt.k = k;
+  bt.max_growth = max_growth;
+  bt.train_err = train_err;
+  bt.growth = growth;
+  bt.status = cand_status;
+  DOPINF_TRY(launch_rollouts(bt, cluster, st));
   select_best<<<1, 32, 0, st>>>(train_err, cand_status, n_cand, w.best);
   DOPINF_TRY(launch_status());
   int best = -1;
@@ -293,9 +346,11 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
   *best_out = best;
   if (best < 0) return DOPINF_E_NO_STABLE;
   const int ir = best / n_pairs, p = best % n_pairs, r = r_list[ir], d = dim_d(r);
-  const double* src = w.Oall + w.o_off[ir] + (size_t)p * r * d;
+  const double* src = w.O[ir] + (size_t)p * r * d;
   DOPINF_CUDA(cudaMemcpy2DAsync(O_best, sizeof(double) * r_max, src, sizeof(double) * r, sizeof(double) * r, d,
                                 cudaMemcpyDeviceToDevice, st));
   DOPINF_CUDA(cudaStreamSynchronize(st));
   return DOPINF_OK;
 }
+
+DOPINF_API int dopinf_tune_learn_cluster(int cluster) { return learn_set_cluster(cluster); }

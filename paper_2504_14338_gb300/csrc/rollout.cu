@@ -2,26 +2,75 @@
 // eq. ROM_quad_time_discrete, or classical RK4 on eq. ROM_quad_time_cont, with the training
 // error and growth criterion of Step IV fused into the time loop.
 //
-// One CTA per candidate.  The operator O = [A | H | c] (r x d) is staged row-major in shared
-// memory (operators up to about 200 KB, i.e. r <= 36); each right-hand-side evaluation
-// builds phi = [q, (q_i q_j)_{i<=j}, 1] in shared memory and forms O phi with one warp per
-// output row.  The time loop is sequential; candidates run concurrently.
+// One thread-block cluster of C CTAs per candidate, every candidate of every r in one launch.
+// CTA rank j of the cluster keeps rows [j*rc, (j+1)*rc) of the operator O = [A | H | c]
+// (rc = ceil(r / C)) row-major in its shared memory.  Each right-hand-side evaluation builds
+// phi = [q, (q_i q_j)_{i<=j}, 1] locally (the state is replicated), forms its rows of O phi
+// with one warp per row, and stores them into the shared memory of every CTA of the cluster
+// (distributed shared memory); a hardware cluster barrier then makes the full vector visible
+// everywhere.  The stage results are double-buffered by step parity, so a CTA that runs ahead
+// never overwrites values a slower peer is still reading.  The RK4 combination, the metrics
+// and the early-exit decision are computed identically in every CTA, so the cluster stays in
+// lockstep without further communication.
 #include "common.cuh"
+#include <cooperative_groups.h>
 #include <math.h>
 
+namespace cg = cooperative_groups;
+
 namespace dopinf {
-
 namespace {
-constexpr int RB = 256;  // threads per rollout CTA
+
+constexpr int RB = 256;  // threads per CTA
 constexpr int NW = RB / 32;
-}  // namespace
 
+struct SmemLayout {
+  size_t o, q, xs, kb, phi, pi, pj, total;
+};
 
-namespace {
+// Shared layout for a CTA holding rc operator rows of width d_max, vectors of r_max.
+__host__ __device__ inline SmemLayout smem_layout(int rc, int r_max, int d_max) {
+  SmemLayout L;
+  size_t off = 0;
+  L.o = off;
+  off += (size_t)rc * d_max * sizeof(double);
+  L.q = off;
+  off += (size_t)r_max * sizeof(double);
+  L.xs = off;
+  off += (size_t)r_max * sizeof(double);
+  L.kb = off;  // [2 step parities][4 stages][r_max]
+  off += (size_t)8 * r_max * sizeof(double);
+  L.phi = off;
+  off += (size_t)d_max * sizeof(double);
+  const int s_max = d_max - r_max - 1 > 0 ? d_max - r_max - 1 : 1;
+  L.pi = off;
+  off += (size_t)s_max * sizeof(unsigned short);
+  L.pj = off;
+  off += (size_t)s_max * sizeof(unsigned short);
+  L.total = (off + 15) / 16 * 16;
+  return L;
+}
 
-__device__ __forceinline__ void rhs_eval(const double* __restrict__ Os, const unsigned short* __restrict__ pi,
-                                         const unsigned short* __restrict__ pj, int r, int d, const double* x,
-                                         double* phi, double* out) {
+// Rows [i0, i1) of O phi, stored into buffer `dst` of every CTA of the cluster.
+__device__ __forceinline__ void eval_rows(cg::cluster_group& cl, const double* Os, int i0, int i1, int d,
+                                          const double* phi, double* dst) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = (int)cl.num_blocks();
+  for (int i = i0 + w; i < i1; i += NW) {
+    const double* row = Os + (size_t)(i - i0) * d;
+    double acc = 0.0;
+    for (int a = lane; a < d; a += 32) acc = fma(row[a], phi[a], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane < C) {
+      double* remote = cl.map_shared_rank(dst, (unsigned)lane);
+      remote[i] = acc;
+    }
+  }
+}
+
+__device__ __forceinline__ void build_phi(const double* x, int r, int d, const unsigned short* pi,
+                                          const unsigned short* pj, double* phi) {
   const int s = d - r - 1;
   for (int a = threadIdx.x; a < d; a += RB) {
     double v;
@@ -33,65 +82,58 @@ __device__ __forceinline__ void rhs_eval(const double* __restrict__ Os, const un
       v = 1.0;
     phi[a] = v;
   }
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = w; i < r; i += NW) {
-    const double* row = Os + (size_t)i * d;
-    double acc = 0.0;
-    for (int a = lane; a < d; a += 32) acc = fma(row[a], phi[a], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[i] = acc;
-  }
-  __syncthreads();
 }
 
-template <bool kMetrics, bool kTraj>
-__global__ void __launch_bounds__(RB) rollout_kernel(RolloutArgs a) {
-  extern __shared__ double sm[];
-  const int r = a.r, d = a.d, s = d - r - 1;
-  const int c = blockIdx.x;
-  // shared layout: O row-major (r*d), q(r) x(r) k1..k4(4r) phi(d) pairs(2*s shorts)
-  double* Os = sm;
-  double* q = sm + (size_t)r * d;
-  double* xs = q + r;
-  double* k1 = xs + r;
-  double* k2 = k1 + r;
-  double* k3 = k2 + r;
-  double* k4 = k3 + r;
-  double* phi = k4 + r;
-  unsigned short* pi = reinterpret_cast<unsigned short*>(phi + d);
-  unsigned short* pj = pi + s;
+__global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int cid = blockIdx.x / C;
+  const RolloutCand cd = bt.cands ? bt.cands[cid] : bt.one;
+  const int r = cd.r, d = cd.d;
+  const int rc = (r + C - 1) / C;
+  const int i0 = rank * rc < r ? rank * rc : r;
+  const int i1 = i0 + rc < r ? i0 + rc : r;
+  const SmemLayout L = smem_layout(bt.rc_max, bt.r_max, bt.d_max);
+  double* Os = reinterpret_cast<double*>(smraw + L.o);
+  double* q = reinterpret_cast<double*>(smraw + L.q);
+  double* xs = reinterpret_cast<double*>(smraw + L.xs);
+  double* kb = reinterpret_cast<double*>(smraw + L.kb);
+  double* phi = reinterpret_cast<double*>(smraw + L.phi);
+  unsigned short* pi = reinterpret_cast<unsigned short*>(smraw + L.pi);
+  unsigned short* pj = reinterpret_cast<unsigned short*>(smraw + L.pj);
   __shared__ int s_stop;
-  if (kMetrics && a.status[a.cand0 + c] != 0) {  // factorisation failed: nothing to roll out
-    if (threadIdx.x == 0) {
-      a.train_err[a.cand0 + c] = INFINITY;
-      a.growth[a.cand0 + c] = INFINITY;
+
+  // a failed factorisation (the same for every CTA of the cluster): nothing to roll out
+  if (bt.metrics && bt.status[cd.cand] != 0) {
+    if (rank == 0 && threadIdx.x == 0) {
+      bt.train_err[cd.cand] = INFINITY;
+      bt.growth[cd.cand] = INFINITY;
     }
     return;
   }
-  const double* Og = a.O + (size_t)c * a.o_stride;
-  for (int64_t e = threadIdx.x; e < (int64_t)r * d; e += RB) {
-    const int i = (int)(e / d), col = (int)(e % d);
-    Os[e] = Og[i + (size_t)col * a.ldo];
+  for (int64_t e = threadIdx.x; e < (int64_t)(i1 - i0) * d; e += RB) {
+    const int i = i0 + (int)(e / d), a = (int)(e % d);
+    Os[e] = cd.O[i + (size_t)a * cd.ldo];
   }
-  const double* Orow = Os;
   for (int i = threadIdx.x; i < r; i += RB) {
-    // pair table: column r + off(i) + (j - i) multiplies x_i x_j
-    int off = i * r - i * (i - 1) / 2;
+    const int off = i * r - i * (i - 1) / 2;  // column r + off(i) + (j - i) multiplies x_i x_j
     for (int j = i; j < r; ++j) {
       pi[off + j - i] = (unsigned short)i;
       pj[off + j - i] = (unsigned short)j;
     }
   }
-  for (int i = threadIdx.x; i < r; i += RB) q[i] = a.q0[i];
+  for (int i = threadIdx.x; i < r; i += RB) q[i] = bt.q0[i];
   if (threadIdx.x == 0) s_stop = 0;
-  __syncthreads();
-  const double dt = a.dt;
+  cl.sync();  // every CTA initialised before any remote store
+
+  const double dt = bt.dt, h2 = 0.5 * dt, h6 = dt / 6.0;
+  const double denom = bt.metrics ? *cd.denom : 1.0;
   double err = 0.0, gnum = 0.0;
   int st = 0;
-  int64_t t = 0;
-  for (;; ++t) {
-    // ---- metrics and output of state t (warp 0) ----
+  for (int64_t t = 0;; ++t) {
+    // ---- metrics and output of state t (warp 0 of every CTA, identical results) ----
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       bool fin = true;
@@ -99,18 +141,19 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutArgs a) {
       for (int i = lane; i < r; i += 32) {
         const double v = q[i];
         fin = fin && isfinite(v);
-        if (kMetrics) {
-          dev = fmax(dev, fabs(v - a.mu[i]));
-          if (t < a.k) {
-            const double h = a.Qhat[i + t * a.ldqh];
+        if (bt.metrics) {
+          dev = fmax(dev, fabs(v - cd.mu[i]));
+          if (t < bt.k) {
+            const double h = bt.Qhat[i + t * bt.ldqh];
             num += (v - h) * (v - h);
             den += h * h;
           }
         }
-        if (kTraj) a.traj[t * r + i] = v;
+        if (bt.traj && rank == 0) bt.traj_out[t * r + i] = v;
       }
       fin = __all_sync(0xffffffffu, fin);
-      if (kMetrics) {
+      if (bt.metrics) {
+#pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
           num += __shfl_xor_sync(0xffffffffu, num, o);
@@ -118,7 +161,7 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutArgs a) {
         }
         if (fin) {
           gnum = fmax(gnum, dev);
-          if (t < a.k) err = fmax(err, sqrt(num / den));
+          if (t < bt.k) err = fmax(err, sqrt(num / den));
         }
       }
       if (lane == 0) {
@@ -126,33 +169,51 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutArgs a) {
         if (!fin) {
           st = 2;
           stop = 1;
-        } else if (kMetrics && gnum / *a.denom >= a.max_growth) {
+        } else if (bt.metrics && gnum / denom >= bt.max_growth) {
           st = 3;
           stop = 1;
         }
-        if (t + 1 >= a.n_steps) stop = 1;
+        if (t + 1 >= bt.n_steps) stop = 1;
         s_stop = stop;
       }
     }
     __syncthreads();
     if (s_stop) break;
-    // ---- advance ----
-    // (products and sums rounded separately, in the order q + (dt/6)((k1 + 2 k2) + 2 k3) + k4)
-    if (a.mode == DOPINF_DISCRETE) {
-      rhs_eval(Orow, pi, pj, r, d, q, phi, k1);
+    double* kp = kb + (size_t)(t & 1) * 4 * bt.r_max;  // this step's stage buffers
+    double* k1 = kp;
+    double* k2 = kp + bt.r_max;
+    double* k3 = kp + 2 * bt.r_max;
+    double* k4 = kp + 3 * bt.r_max;
+    if (bt.mode == DOPINF_DISCRETE) {
+      build_phi(q, r, d, pi, pj, phi);
+      __syncthreads();
+      eval_rows(cl, Os, i0, i1, d, phi, k1);
+      cl.sync();
       for (int i = threadIdx.x; i < r; i += RB) q[i] = k1[i];
     } else {
-      const double h2 = 0.5 * dt, h6 = dt / 6.0;
-      rhs_eval(Orow, pi, pj, r, d, q, phi, k1);
+      // products and sums rounded separately, in the order q + (dt/6)(((k1 + 2 k2) + 2 k3) + k4)
+      build_phi(q, r, d, pi, pj, phi);
+      __syncthreads();
+      eval_rows(cl, Os, i0, i1, d, phi, k1);
+      cl.sync();
       for (int i = threadIdx.x; i < r; i += RB) xs[i] = __dadd_rn(q[i], __dmul_rn(h2, k1[i]));
       __syncthreads();
-      rhs_eval(Orow, pi, pj, r, d, xs, phi, k2);
+      build_phi(xs, r, d, pi, pj, phi);
+      __syncthreads();
+      eval_rows(cl, Os, i0, i1, d, phi, k2);
+      cl.sync();
       for (int i = threadIdx.x; i < r; i += RB) xs[i] = __dadd_rn(q[i], __dmul_rn(h2, k2[i]));
       __syncthreads();
-      rhs_eval(Orow, pi, pj, r, d, xs, phi, k3);
+      build_phi(xs, r, d, pi, pj, phi);
+      __syncthreads();
+      eval_rows(cl, Os, i0, i1, d, phi, k3);
+      cl.sync();
       for (int i = threadIdx.x; i < r; i += RB) xs[i] = __dadd_rn(q[i], __dmul_rn(dt, k3[i]));
       __syncthreads();
-      rhs_eval(Orow, pi, pj, r, d, xs, phi, k4);
+      build_phi(xs, r, d, pi, pj, phi);
+      __syncthreads();
+      eval_rows(cl, Os, i0, i1, d, phi, k4);
+      cl.sync();
       for (int i = threadIdx.x; i < r; i += RB) {
         const double sum = __dadd_rn(__dadd_rn(__dadd_rn(k1[i], 2.0 * k2[i]), 2.0 * k3[i]), k4[i]);
         q[i] = __dadd_rn(q[i], __dmul_rn(h6, sum));
@@ -160,41 +221,51 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutArgs a) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    if (kMetrics) {
-      const int ci = a.cand0 + c;
-      a.status[ci] = st;
-      a.train_err[ci] = st == 0 ? err : INFINITY;
-      a.growth[ci] = st == 2 ? INFINITY : gnum / *a.denom;
+  cl.sync();  // no CTA leaves while a peer may still store into its shared memory
+  if (rank == 0 && threadIdx.x == 0) {
+    if (bt.metrics) {
+      bt.status[cd.cand] = st;
+      bt.train_err[cd.cand] = st == 0 ? err : INFINITY;
+      bt.growth[cd.cand] = st == 2 ? INFINITY : gnum / denom;
     }
-    if (kTraj && a.finite) *a.finite = st == 2 ? 0 : 1;
+    if (bt.traj && bt.finite) *bt.finite = st == 2 ? 0 : 1;
   }
 }
 
-size_t rollout_smem(int r, int d) {
-  const int s = d - r - 1;
-  return ((size_t)r * d + 6 * (size_t)r + d) * sizeof(double) + 2 * (size_t)s * sizeof(unsigned short) + 16;
-}
+constexpr size_t kRolloutSmemMax = 200 * 1024;
 
 }  // namespace
 
-// Shared memory budget: the operator is staged only when it fits.
-constexpr size_t kRolloutSmemMax = 200 * 1024;
+size_t rollout_smem_bytes(int cluster, int r_max, int d_max) {
+  return smem_layout((r_max + cluster - 1) / cluster, r_max, d_max).total;
+}
 
-int launch_rollouts(const RolloutArgs& a, int n_cand, bool metrics, bool traj, cudaStream_t st) {
-  const size_t smem = rollout_smem(a.r, a.d);
-  if (smem > kRolloutSmemMax) return DOPINF_E_UNSUPPORTED;  // operator larger than shared memory
-  if (metrics && !traj) {
-    DOPINF_CUDA(cudaFuncSetAttribute(rollout_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kRolloutSmemMax));
-    rollout_kernel<true, false><<<n_cand, RB, smem, st>>>(a);
-  } else if (!metrics && traj) {
-    DOPINF_CUDA(cudaFuncSetAttribute(rollout_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kRolloutSmemMax));
-    rollout_kernel<false, true><<<n_cand, RB, smem, st>>>(a);
-  } else {
-    return DOPINF_E_ARG;
-  }
+int rollout_cluster_size(int r_max, int d_max, int want) {
+  int c = 1;
+  while (c < want && c < 8) c *= 2;
+  while (c < 8 && rollout_smem_bytes(c, r_max, d_max) > kRolloutSmemMax) c *= 2;
+  return rollout_smem_bytes(c, r_max, d_max) <= kRolloutSmemMax ? c : 0;
+}
+
+int launch_rollouts(RolloutBatch bt, int cluster, cudaStream_t st) {
+  if (cluster < 1 || cluster > 8 || bt.n_cand < 1) return DOPINF_E_ARG;
+  bt.rc_max = (bt.r_max + cluster - 1) / cluster;
+  const size_t smem = rollout_smem_bytes(cluster, bt.r_max, bt.d_max);
+  if (smem > kRolloutSmemMax) return DOPINF_E_UNSUPPORTED;
+  DOPINF_CUDA(cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRolloutSmemMax));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(bt.n_cand * cluster), 1, 1);
+  cfg.blockDim = dim3(RB, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  DOPINF_CUDA(cudaLaunchKernelEx(&cfg, rollout_kernel, bt));
   return launch_status();
 }
 
@@ -206,17 +277,25 @@ DOPINF_API int dopinf_rollout(const double* O, int r, int64_t ldo, const double*
                               double dt, double* Qtilde, int* finite, void* stream) {
   if (!O || !q0 || !Qtilde || r < 1 || r > 255 || ldo < r || n_steps < 1) return DOPINF_E_ARG;
   if (mode != DOPINF_DISCRETE && mode != DOPINF_CONTINUOUS_RK4) return DOPINF_E_ARG;
-  RolloutArgs a = {};
-  a.O = O;
-  a.o_stride = 0;
-  a.ldo = ldo;
-  a.r = r;
-  a.d = r + r * (r + 1) / 2 + 1;
-  a.mode = mode;
-  a.dt = dt;
-  a.n_steps = n_steps;
-  a.q0 = q0;
-  a.traj = Qtilde;
-  a.finite = finite;
-  return launch_rollouts(a, 1, false, true, as_stream(stream));
+  const int d = r + r * (r + 1) / 2 + 1;
+  const int cluster = rollout_cluster_size(r, d, r >= 16 ? 4 : 1);
+  if (!cluster) return DOPINF_E_UNSUPPORTED;
+  RolloutBatch bt = {};
+  bt.cands = nullptr;  // the single candidate travels inside the launch arguments
+  bt.one.O = O;
+  bt.one.ldo = ldo;
+  bt.one.r = r;
+  bt.one.d = d;
+  bt.one.cand = 0;
+  bt.n_cand = 1;
+  bt.r_max = r;
+  bt.d_max = d;
+  bt.mode = mode;
+  bt.dt = dt;
+  bt.n_steps = n_steps;
+  bt.q0 = q0;
+  bt.traj = 1;
+  bt.traj_out = Qtilde;
+  bt.finite = finite;
+  return launch_rollouts(bt, cluster, as_stream(stream));
 }

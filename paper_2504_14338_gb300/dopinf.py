@@ -17,11 +17,11 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdopinf.so")
 
-OK, E_ARG, E_CUDA, E_NONFINITE, E_RANK, E_NO_STABLE, E_UNSUPPORTED = 0, -1, -2, -4, -6, -7, -9
+OK, E_ARG, E_CUDA, E_NONFINITE, E_RANK, E_NO_STABLE, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -4, -6, -7, -8, -9
 FLAG_NONFINITE, FLAG_ZERO_SCALE = 1, 2
 F64, F32 = 0, 1
 CENTER, SCALE = 1, 2
-GRAM_FP64, GRAM_BF16X3 = 0, 1
+GRAM_FP64, GRAM_BF16X4 = 0, 1
 DISCRETE, CONTINUOUS_RK4 = 0, 1
 
 _c_i64 = ctypes.c_int64
@@ -61,6 +61,8 @@ def _load():
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, _c_i64, ctypes.c_double, _c_p, _c_p, _c_p,
                                         ctypes.POINTER(ctypes.c_int), _c_p, _c_p, _c_sz, _c_p]),
+        "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
+        "dopinf_tune_learn_cluster": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_rollout": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_p, _c_i64, ctypes.c_int,
                                           ctypes.c_double, _c_p, _c_p, _c_p]),
     }
@@ -166,6 +168,16 @@ def dopinf_gram(Q, mode=GRAM_FP64, D=None, accumulate=False, ws=None, stream=Non
     _check("dopinf_gram", lib.dopinf_gram(_ptr(Q), _dtype_code(Q), n, k, ldq, mode, int(accumulate), _ptr(D),
                                           D.stride(0), _ptr(buf), nb, _stream(stream)))
     return D
+
+
+def dopinf_tune_gram_chunk(rows=0):
+    """Sets (rows > 0) or queries the FP32 accumulation chunk of the split Gram; returns the previous value."""
+    return int(lib.dopinf_tune_gram_chunk(int(rows)))
+
+
+def dopinf_tune_learn_cluster(cluster=0):
+    """Sets (1, 2, 4, 8) or queries the rollout cluster size of dopinf_learn; returns the previous value."""
+    return int(lib.dopinf_tune_learn_cluster(int(cluster)))
 
 
 def dopinf_reduce(D, r_cap, energy_target=0.9996, r_fixed=0, ws=None, stream=None):

@@ -187,8 +187,12 @@ def snapshots_torch(w: Workload, device, col_major=True):
     g = torch.Generator(device=device)
     g.manual_seed(w.seed)
     G = torch.randn(w.n, w.r_true, generator=g, device=device, dtype=torch.float64)
-    L, _ = torch.linalg.qr(G)
-    del G
+    # orthonormal columns by CholeskyQR applied twice (matrix products on the device, the
+    # r_true x r_true Cholesky factor on the host)
+    for _ in range(2):
+        R = np.linalg.cholesky((G.T @ G).cpu().numpy()).T
+        G = G @ torch.from_numpy(np.linalg.inv(R)).to(device)
+    L = G
     Mn = X if w.decay <= 0 else _decay_shaper(X, w.decay) @ X
     M = torch.from_numpy(Mn).to(device)
     noise_std = w.noise_rel * np.linalg.norm(Mn) / np.sqrt(w.n * w.k)  # ||L M||_F = ||M||_F

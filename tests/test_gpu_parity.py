@@ -119,6 +119,43 @@ def test_gram_row_partition_accumulates(dp):
     assert np.all(np.abs(D.cpu().numpy() - ref) <= bound)
 
 
+@pytest.mark.parametrize("n,k,dtype", [(100_003, 300, "f32"), (40_000, 257, "f64"), (5000, 64, "f32"), (70, 17, "f64")])
+def test_gram_bf16x4_vs_oracle(dp, n, k, dtype):
+    # two BF16 slices per value leave |e| <= 2^-17 |x| out, with signs varying from row to
+    # row.  Each 64-row chunk is summed by 16 MMAs of which 4 add to a large accumulator, each
+    # rounding toward zero by at most one ulp: <= 4 * 2^-23 of the chunk's sum of |terms|,
+    # about 5e-7; the chunks are then summed with TwoSum (error ~2^-44).  Allowed: 2e-6.
+    rng = np.random.default_rng(n + 7 * k)
+    Qn = rng.standard_normal((n, k)) * np.exp(rng.uniform(-3, 3, k))
+    if dtype == "f32":
+        Qn = Qn.astype(np.float32)
+    Q = to_dev(dp, Qn)
+    D = dp.dopinf_gram(Q, mode=dp.GRAM_BF16X4).cpu().numpy()
+    ref = O.gram(Qn)
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    rel = np.abs(D - ref) / scale
+    diag = (np.diag(D) - np.diag(ref)) / np.diag(ref)
+    print("bf16x4 max rel", rel.max(), "median", np.median(rel), "diag bias", diag.mean())
+    assert rel.max() <= 2e-6
+    assert np.array_equal(D, D.T)
+    assert np.array_equal(D, dp.dopinf_gram(Q, mode=dp.GRAM_BF16X4).cpu().numpy())  # reproducible
+
+
+def test_gram_bf16x4_eigenvalues_within_target(dp):
+    # a lifted spectrum lambda_i ~ i^-3 (the detonation-shaped case): the split Gram's
+    # leading eigenvalues match the FP64 oracle within 1e-6 lambda_1
+    w = synth.Workload("t", 4, 25_000, 400, 60, decay=3.0, noise_rel=1e-6, dtype="f32", seed=77)
+    Qn, _ = synth.snapshots_numpy(w)
+    Qt, _, _, _ = O.transform(Qn, w.var_row_offsets())
+    ref = O.gram(Qt)
+    D = dp.dopinf_gram(to_dev(dp, Qt), mode=dp.GRAM_BF16X4).cpu().numpy()
+    lam_ref = np.linalg.eigvalsh(ref)[::-1]
+    lam = np.linalg.eigvalsh(D)[::-1]
+    err = np.max(np.abs(lam[:50] - lam_ref[:50])) / lam_ref[0]
+    print("top-50 eigenvalue error / lambda_1", err)
+    assert err <= 1e-6
+
+
 # ------------------------------------------------------------------------------ Step III reduce
 def _pipeline_D(seed=1234, n_vars=2, n_per=2048, k=200, r_true=6, scales=()):
     w = synth.Workload("t", n_vars, n_per, k, r_true, var_scales=scales, seed=seed)
