@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--stage", default="all", choices=["all", "gram", "learn"],
                    help="gram / learn: time only that stage (for profiling)")
     p.add_argument("--n-per-var", type=int, default=0, help="override rows per variable (smaller case)")
+    p.add_argument("--no-split", action="store_true", help="skip the split-precision Gram measurement")
+    p.add_argument("--no-sequential", action="store_true", help="skip the sequential grid-search baseline")
     return p.parse_args()
 
 
@@ -158,6 +160,91 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------ extras
+def split_gram_measure(dp, synth, dev, frac=16):
+    """Split-precision (BF16x4) Gram at the detonation shape against the GPU's FP64 path.
+
+    The FP64 Gram of the full 12M x 2000 matrix would take ~45 s, so both Grams are also
+    formed on the first n/frac rows (a row block): there the errors are measured, and the
+    FP64 time is scaled by frac (its cost is linear in n)."""
+    import torch
+    w = synth.WORKLOADS["rdre"]
+    QT = synth.snapshots_torch(w, dev)
+    Q = QT.t()
+    stream = torch.cuda.current_stream()
+    ws = dp.Workspace(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_transform = ev[0].elapsed_time(ev[1])
+    D = dp.dopinf_gram(Q, mode=dp.GRAM_BF16X4, ws=ws)   # warm-up
+    times = []
+    for _ in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dp.dopinf_gram(Q, mode=dp.GRAM_BF16X4, D=D, ws=ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    t_split = float(np.mean(times))
+    ns = w.n // frac
+    Qs = Q[:ns]
+    Ds = dp.dopinf_gram(Qs, mode=dp.GRAM_BF16X4, ws=ws).cpu().numpy()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    D64 = dp.dopinf_gram(Qs, ws=ws)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t64_sub = a.elapsed_time(b)
+    D64 = D64.cpu().numpy()
+    del Q, QT, D
+    torch.cuda.empty_cache()
+    lam64 = np.linalg.eigvalsh(D64)[::-1]
+    lams = np.linalg.eigvalsh(Ds)[::-1]
+    eig_err = float(np.max(np.abs(lams[:100] - lam64[:100])) / lam64[0])
+    # Qhat error of the split path against the FP64 path (same reduction code, r = 100)
+    red64 = dp.dopinf_reduce(torch.from_numpy(D64).to(dev), r_cap=100, r_fixed=100)
+    reds = dp.dopinf_reduce(torch.from_numpy(Ds).to(dev), r_cap=100, r_fixed=100)
+    q64 = red64["Qhat"].cpu().numpy()
+    qs = reds["Qhat"].cpu().numpy()
+    qerr = float(np.linalg.norm(qs - q64) / np.linalg.norm(q64))
+    qerr20 = float(np.linalg.norm(qs[:20] - q64[:20]) / np.linalg.norm(q64[:20]))
+    useful = w.n * w.k * (w.k + 1)
+    executed = 4 * 2 * w.n * w.k * (w.k + 128) / 2   # 4 products over the 128x128 upper tiles
+    bf16 = 1978.2
+    try:
+        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    except (OSError, KeyError):
+        pass
+    return {"workload": "rdre: n=8x1.5M=12M, k=2000, FP32 (96 GB), lambda_i ~ i^-3, noise 1e-6",
+            "split_ms": t_split, "useful_tflops": useful / t_split / 1e9,
+            "executed_tflops": executed / t_split / 1e9, "frac_of_bf16_peak": executed / t_split / 1e9 / bf16,
+            "fp64_ms_estimated": t64_sub * frac, "fp64_ms_on_1_of_%d_rows" % frac: t64_sub,
+            "speedup_vs_fp64": t64_sub * frac / t_split,
+            "top100_eig_err_rel_lambda1": eig_err, "qhat_err_r100": qerr, "qhat_err_r20": qerr20,
+            "errors_measured_on": "first n/%d rows" % frac, "transform_ms": t_transform,
+            "transform_gbs": 3 * w.n * w.k * 4 / t_transform / 1e6}
+
+
+def sequential_learn_measure(dp, Qhat, w, mode):
+    """The grid search one candidate at a time (one dopinf_learn call per (r, beta1, beta2),
+    one CTA per rollout): the unbatched baseline of the batched learn step."""
+    import torch
+    prev = dp.dopinf_tune_learn_cluster(1)
+    ws = dp.Workspace(Qhat.device)
+    t0 = time.perf_counter()
+    for r in w.r_list:
+        for b1 in w.beta1s():
+            for b2 in w.beta2s():
+                dp.dopinf_learn(Qhat, [r], [b1], [b2], w.n_steps, mode=mode, dt=w.snap_dt, ws=ws)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dp.dopinf_tune_learn_cluster(prev)
+    return dt * 1e3
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -227,6 +314,8 @@ def main():
                               "valid": int((st == 0).sum()), "n_cand": int(st.size)}), flush=True)
         return
 
+    last = {}
+
     def step(record=False):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         e[0].record(stream)
@@ -235,6 +324,7 @@ def main():
         D = dp.dopinf_gram(Q, ws=ws)
         e[2].record(stream)
         red = dp.dopinf_reduce(D, r_cap=r_max, r_fixed=r_max, ws=ws)
+        last["red"] = red
         e[3].record(stream)
         res = dp.dopinf_learn(red["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode, dt=w.snap_dt, ws=ws)
         e[4].record(stream)
@@ -265,6 +355,7 @@ def main():
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
+    red_last = last["red"]
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     names = ["transform", "gram", "reduce", "learn"]
@@ -311,6 +402,15 @@ def main():
         per, desc, wall = oracle_sample(w)
         cpu = {"value": 1.0 / per, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
                "sample_wall_s": wall}
+    split = None
+    if rank == 0 and not args.no_split and args.stage == "all" and not args.n_per_var:
+        del QT, Q
+        torch.cuda.empty_cache()
+        split = split_gram_measure(dp, synth, dev)
+    seq = None
+    if rank == 0 and not args.no_sequential:
+        seq_ms = sequential_learn_measure(dp, red_last["Qhat"], w, mode)
+        seq = {"sequential_ms": seq_ms, "batched_ms": stage["learn"], "speedup": seq_ms / stage["learn"]}
     if rank == 0:
         best = res["best"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -319,7 +419,7 @@ def main():
                 "stages_ms": stage, "gram_tflops_fp64": gram_tf, "learn_s": stage["learn"] / 1e3,
                 "best": {"index": best, "r": res.get("r"), "beta1": res.get("beta1"), "beta2": res.get("beta2")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
-                "clocks": ck}
+                "clocks": ck, "split_gram": split, "learn_vs_sequential": seq}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
