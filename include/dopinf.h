@@ -120,6 +120,29 @@ int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int
                 void* stream);
 
 /* ------------------------------------------------------------------------------------
+ * Allocation-free FP64 Gram.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory (code running inside a memory pool or an
+ * allocator callback, plugins barred from the device allocator, code that runs while
+ * another component is building a CUDA graph).  It computes exactly what
+ * dopinf_gram(..., DOPINF_GRAM_FP64, ...) computes, same arguments minus the workspace,
+ * with its scratch (the split-K partial tiles) in a fixed 32 MiB array of device memory
+ * that every GPU loading this library holds until the process exits
+ * (dopinf_gram_noalloc_scratch_bytes() returns the size).
+ *  - Limit: k <= 2816 (the 64 x 64 upper tiles of D must fit the array); larger k returns
+ *    DOPINF_E_UNSUPPORTED before anything is launched.  n >= 1.
+ *  - The first call on each device resolves the array's device address on that device
+ *    (the device must be current); make that first call before any stream capture, and not
+ *    from several host threads at once.
+ *  - Every call on a device shares the one array and leaves its last contents there; calls
+ *    that overlap on the GPU (different streams, no ordering between them) race on it and
+ *    give wrong results.  Calls on one stream are safe.  Asynchronous; D follows the same
+ *    layout and symmetry rules as dopinf_gram.
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_gram_noalloc_scratch_bytes(void);
+int dopinf_gram_fp64_noalloc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate,
+                             double* D, int64_t ldd, void* stream);
+
+/* ------------------------------------------------------------------------------------
  * Step III eigensolve and projection (eqs. mos_Sigma_W, ret_energy, MoS_POD_basis,
  * dOpInf_projection).  Symmetric eigendecomposition of D (k x k FP64, ldd), leading
  * r_cap eigenpairs in descending order; sign of each eigenvector: its largest-magnitude

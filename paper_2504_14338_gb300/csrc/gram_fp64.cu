@@ -208,3 +208,70 @@ DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64
   if (mode == DOPINF_GRAM_BF16X4) return gram_tc(Q, dtype, n, k, ldq, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
   return tn_product(Q, ldq, Q, ldq, dtype, n, k, k, 1, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
 }
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free FP64 Gram: the same kernels with their split-K partials in a fixed
+// file-scope device array instead of a caller workspace.  For callers that cannot allocate
+// device memory: code running inside a memory pool or an allocator callback, plugins that
+// must not touch the device allocator, and code that runs while a CUDA graph is being
+// built by someone else.  The array (kNoAllocScratchBytes) lives on every GPU that loads
+// this library until the process exits.
+// ------------------------------------------------------------------------------------------
+namespace dopinf {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB per device
+constexpr int kNoAllocMaxUnits = (int)(kNoAllocScratchBytes / (TM * TN * sizeof(double)));
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
+
+constexpr int kNoAllocMaxDevices = 128;
+// Device address of g_noalloc_scratch per device ordinal.  In host code the symbol name is a
+// host-side stand-in, not a device address, so it is resolved once per device with
+// cudaGetSymbolAddress while that device is current.
+void* g_noalloc_addr[kNoAllocMaxDevices];
+
+}  // namespace
+}  // namespace dopinf
+
+DOPINF_API size_t dopinf_gram_noalloc_scratch_bytes(void) { return dopinf::kNoAllocScratchBytes; }
+
+DOPINF_API int dopinf_gram_fp64_noalloc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate,
+                                        double* D, int64_t ldd, void* stream) {
+  using namespace dopinf;
+  if (n < 1 || k < 1 || ldq < n || ldd < k || !D || !Q) return DOPINF_E_ARG;
+  if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
+  // plan: as the workspace path, with the row split reduced until the partials fit the array
+  TnPlan p = make_plan(n, k, k, 1);
+  if (p.ntiles > kNoAllocMaxUnits) return DOPINF_E_UNSUPPORTED;  // k too large for the fixed scratch
+  if (p.units > kNoAllocMaxUnits) {
+    const int splits = kNoAllocMaxUnits / p.ntiles;
+    int64_t rps = (n + splits - 1) / splits;
+    rps = (rps + BK - 1) / BK * BK;
+    p.rows_per_split = rps;
+    p.splits = (int)((n + rps - 1) / rps);
+    p.units = p.ntiles * p.splits;
+    p.grid = p.units < kSlots ? p.units : kSlots;
+  }
+  int dev = 0;
+  DOPINF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return DOPINF_E_UNSUPPORTED;
+  if (!g_noalloc_addr[dev]) {  // first call on this device: resolve the array's device address
+    void* addr = nullptr;
+    DOPINF_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+    g_noalloc_addr[dev] = addr;
+  }
+  double* part = static_cast<double*>(g_noalloc_addr[dev]);
+  cudaStream_t st = as_stream(stream);
+  if (dtype == DOPINF_F64)
+    tn_partial<double><<<p.grid, NT, 0, st>>>(static_cast<const double*>(Q), ldq, static_cast<const double*>(Q), ldq,
+                                              n, k, k, p.rows_per_split, p.tiles_m, p.tiles_n, 1, p.ntiles, p.units,
+                                              part);
+  else
+    tn_partial<float><<<p.grid, NT, 0, st>>>(static_cast<const float*>(Q), ldq, static_cast<const float*>(Q), ldq, n,
+                                             k, k, p.rows_per_split, p.tiles_m, p.tiles_n, 1, p.ntiles, p.units,
+                                             part);
+  DOPINF_TRY(launch_status());
+  tn_reduce<<<dim3(p.ntiles, TM * TN / NT), NT, 0, st>>>(part, p.splits, p.ntiles, p.tiles_m, p.tiles_n, 1, k, k,
+                                                         accumulate, D, ldd);
+  return launch_status();
+}
