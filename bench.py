@@ -44,6 +44,7 @@ def parse():
                    help="gram / learn: time only that stage (for profiling)")
     p.add_argument("--n-per-var", type=int, default=0, help="override rows per variable (smaller case)")
     p.add_argument("--no-split", action="store_true", help="skip the split-precision Gram measurement")
+    p.add_argument("--gram-mode", default="fp64", choices=["fp64", "bf16x4", "ozaki"], help="Gram mode of --stage gram")
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential grid-search baseline")
     return p.parse_args()
 
@@ -280,21 +281,22 @@ def main():
 
     ev = {}
     if args.stage == "gram":
+        gmode = {"fp64": dp.GRAM_FP64, "bf16x4": dp.GRAM_BF16X4, "ozaki": dp.GRAM_OZAKI_FP64}[args.gram_mode]
         dp.dopinf_transform(Q, offs, ws=ws)
         D = torch.zeros(w.k, w.k, dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
-            dp.dopinf_gram(Q, D=D, ws=ws)
+            dp.dopinf_gram(Q, mode=gmode, D=D, ws=ws)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(args.steps):
-            dp.dopinf_gram(Q, D=D, ws=ws)
+            dp.dopinf_gram(Q, mode=gmode, D=D, ws=ws)
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
         if rank == 0:
-            print(json.dumps({"stage": "gram", "n": w.n, "k": w.k, "ms": ms,
-                              "tflops": w.n * w.k * (w.k + 1) / ms / 1e9}), flush=True)
+            print(json.dumps({"stage": "gram", "mode": args.gram_mode, "n": w.n, "k": w.k, "ms": ms,
+                              "useful_tflops": w.n * w.k * (w.k + 1) / ms / 1e9}), flush=True)
         return
     if args.stage == "learn":
         dp.dopinf_transform(Q, offs, ws=ws)

@@ -56,7 +56,8 @@ enum dopinf_dtype { DOPINF_F64 = 0, DOPINF_F32 = 1 };
 
 enum dopinf_gram_mode {
   DOPINF_GRAM_FP64 = 0,      /* FP64 FMA over every row (the plain path) */
-  DOPINF_GRAM_BF16X4 = 1     /* two BF16 slices per value, four tensor-core products (see dopinf_gram) */
+  DOPINF_GRAM_BF16X4 = 1,    /* two BF16 slices per value, four tensor-core products (see dopinf_gram) */
+  DOPINF_GRAM_OZAKI_FP64 = 2 /* FP64-accurate: exact integer digit products on the tensor cores */
 };
 
 enum dopinf_rom_mode {
@@ -66,6 +67,9 @@ enum dopinf_rom_mode {
 
 /* Human-readable name of a status code (static storage). */
 const char* dopinf_status_string(int status);
+/* Text of the last CUDA error behind a DOPINF_E_CUDA in this host thread ("" if none);
+ * valid until the next failing call of the same thread. */
+const char* dopinf_last_error(void);
 
 /* ------------------------------------------------------------------------------------
  * Step II (Section 3.3): centre each row by its temporal mean, then divide each variable
@@ -104,8 +108,15 @@ int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
  *   over 64-row chunks, a compensated FP32 (TwoSum) running sum per work unit, FP64 sum of
  *   the units (|e| <= 2^-17 |x|).  Requires k <= 65535.  Synchronises the stream; returns
  *   DOPINF_E_TIMEOUT if an internal bounded wait expired (D is then not valid).
+ * DOPINF_GRAM_OZAKI_FP64: column a is scaled by 2^-s_a (s_a bounding its max-abs) and cut
+ *   into 8 integer digits of 7 bits (exact in BF16): x = 2^s_a sum_i d_i 2^(-7 i) + e,
+ *   |e| <= 2^(s_a - 57).  The 36 digit products of weight 2..9 are summed on the tensor cores
+ *   in row chunks whose partial sums are integers below 2^24 (exact), carried exactly by FP32
+ *   TwoSum pairs and combined in FP64: an FP64-accurate D (the method of Ozaki et al. 2012).
+ *   Requires k <= 65535.  Synchronises the stream; may return DOPINF_E_TIMEOUT.
  * Workspace: dopinf_gram_workspace(n, k, dtype, mode) bytes (BF16X4: 4 n k bytes of
- *   slices plus the per-unit FP64 partial tiles).
+ *   slices plus the per-unit FP64 partial tiles; OZAKI_FP64: 16 n k bytes of digits plus
+ *   8 partial tiles per unit).
  * ------------------------------------------------------------------------------------ */
 size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode);
 /* Tuning of DOPINF_GRAM_BF16X4: rows summed by one FP32 tensor-memory accumulator before it
@@ -214,6 +225,38 @@ int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
  * ------------------------------------------------------------------------------------ */
 int dopinf_rollout(const double* O, int r, int64_t ldo, const double* q0, int64_t n_steps,
                    int mode, double dt, double* Qtilde, int* finite, void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Learned proposal of (beta1, beta2, r).  The paper picks (beta1, beta2) by the grid search
+ * of Section 3.5 and r by the retained energy of eq. ret_energy; this network proposes the
+ * grid indices from statistics of the reduced data, and the grid search stays its fallback.
+ * Network: 64 -> 256 -> 256 -> 256 -> H (GELU, exact erf form), H = head_sizes[0] +
+ * head_sizes[1] + head_sizes[2] (beta1 index, beta2 index, r index).  Parameters: FP32,
+ * flat [W1 (256 x 64 row-major), b1, W2 (256 x 256), b2, W3, b3, W4 (H x 256), b4]; weights are
+ * rounded to BF16 (nearest even) where used; FP32 activations and accumulation.
+ * ------------------------------------------------------------------------------------ */
+/* The 64 features of one reduced system, in FP32 (device, 64 floats):
+ *   f[0:32]  log10(max(lambda_i / lambda_1, 1e-30)), i = 2..33 (-30 if absent);
+ *   f[32:36] log10(max(1 - sum_{i<=r} lambda_i / trace, 1e-30)), r = 5, 10, 20, 30;
+ *   f[36:52] log10(rms_t(q_j[t+1] - q_j[t]) / rms_t(q_j[t])), modes j = 0..15 (0 if absent);
+ *   f[52:63] mean(q_j^4) / mean(q_j^2)^2 - 1.5, modes j = 0..10 (0 if absent);
+ *   f[63]    log10(k).
+ * eigvals: device, n_eig descending eigenvalues; trace > 0 (host); Qhat: r_max x k, ld ldqh. */
+int dopinf_proposal_features(const double* eigvals, int n_eig, double trace, const double* Qhat, int r_max,
+                             int64_t k, int64_t ldqh, float* features, void* stream);
+size_t dopinf_mlp_param_count(int n_out);
+size_t dopinf_mlp_workspace(int batch, int n_out);
+/* logits (device, batch x n_out row-major) of X (device, batch x 64 row-major). */
+int dopinf_mlp_forward(const float* params, int n_out, const float* X, int batch, float* logits, void* ws,
+                       size_t ws_bytes, void* stream);
+/* One training step: forward, mean over the batch of the summed per-head softmax
+ * cross-entropies (loss, device float, optional), backward, and (lr > 0) an Adam update
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with step >= 1) of params with moments
+ * adam_m, adam_v (device, param_count floats each).  labels: device, batch x 3 ints.
+ * grad_out (optional, device, param_count floats) receives the gradient.  head_sizes: host. */
+int dopinf_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const int* head_sizes,
+                          const float* X, const int* labels, int batch, float* loss, float* grad_out, void* ws,
+                          size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

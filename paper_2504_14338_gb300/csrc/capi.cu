@@ -1,5 +1,17 @@
-// Status strings of the C ABI.
+// Status strings of the C ABI and the last CUDA error met.
 #include "common.cuh"
+#include <stdio.h>
+
+namespace dopinf {
+namespace {
+thread_local char g_last_error[256] = "";
+}
+void set_last_error(const char* where, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+}
+}  // namespace dopinf
+
+DOPINF_API const char* dopinf_last_error(void) { return dopinf::g_last_error; }
 
 DOPINF_API const char* dopinf_status_string(int status) {
   switch (status) {

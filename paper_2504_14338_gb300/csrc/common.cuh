@@ -30,10 +30,22 @@ struct Carver {
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? DOPINF_OK : DOPINF_E_CUDA; }
+// Text of the last CUDA error the library met (per host thread), for dopinf_last_error().
+void set_last_error(const char* where, cudaError_t e);
+
+inline int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DOPINF_OK;
+  set_last_error("CUDA call", e);
+  return DOPINF_E_CUDA;
+}
 
 // Launch-error check after a kernel launch (does not synchronise).
-inline int launch_status() { return cuda_status(cudaGetLastError()); }
+inline int launch_status() {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return DOPINF_OK;
+  set_last_error("kernel launch", e);
+  return DOPINF_E_CUDA;
+}
 
 inline bool misaligned(const void* p, size_t a = kAlign) {
   return (reinterpret_cast<uintptr_t>(p) % a) != 0;
@@ -61,6 +73,10 @@ int tn_product(const void* A, int64_t lda, const void* B, int64_t ldb, int dtype
 // Split-precision Gram on the tensor cores (gram_tc.cu); synchronises the stream.
 size_t gram_tc_workspace(int64_t n, int64_t k);
 int64_t gram_tc_set_chunk_rows(int64_t rows);
+// FP64-accurate Gram from exact integer digit products on the tensor cores (gram_ozaki.cu).
+size_t gram_ozaki_workspace(int64_t n, int64_t k);
+int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
+               void* ws, size_t ws_bytes, cudaStream_t st);
 int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
             void* ws, size_t ws_bytes, cudaStream_t st);
 

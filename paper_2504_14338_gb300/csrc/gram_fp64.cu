@@ -190,6 +190,7 @@ DOPINF_API size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mod
   (void)dtype;
   if (n < 0 || k < 1) return 0;
   if (mode == DOPINF_GRAM_BF16X4) return gram_tc_workspace(n, k);
+  if (mode == DOPINF_GRAM_OZAKI_FP64) return gram_ozaki_workspace(n, k);
   if (mode != DOPINF_GRAM_FP64) return 0;
   return tn_workspace(n, k, k, 1);
 }
@@ -199,13 +200,16 @@ DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64
                            void* stream) {
   if (n < 0 || k < 1 || ldq < (n > 1 ? n : 1) || ldd < k || !D || (n > 0 && !Q)) return DOPINF_E_ARG;
   if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
-  if (mode != DOPINF_GRAM_FP64 && mode != DOPINF_GRAM_BF16X4) return DOPINF_E_UNSUPPORTED;
+  if (mode != DOPINF_GRAM_FP64 && mode != DOPINF_GRAM_BF16X4 && mode != DOPINF_GRAM_OZAKI_FP64)
+    return DOPINF_E_UNSUPPORTED;
   if (n == 0) {
     if (accumulate) return DOPINF_OK;
     return cuda_status(cudaMemset2DAsync(D, ldd * sizeof(double), 0, k * sizeof(double), k,
                                          as_stream(stream)));
   }
   if (mode == DOPINF_GRAM_BF16X4) return gram_tc(Q, dtype, n, k, ldq, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
+  if (mode == DOPINF_GRAM_OZAKI_FP64)
+    return gram_ozaki(Q, dtype, n, k, ldq, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
   return tn_product(Q, ldq, Q, ldq, dtype, n, k, k, 1, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
 }
 

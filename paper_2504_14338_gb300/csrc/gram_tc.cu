@@ -13,17 +13,20 @@
 // 64 rows), the three small slice products of a stage are issued before the large H^T H one
 // (only 4 MMAs then add to a large accumulator), and each chunk sum is added to an FP32
 // (hi, lo) pair kept in tensor memory with Knuth's TwoSum, which carries the running sum to
-// about 2^-44.  At the end of a work unit (tile, row range) hi + lo is written in FP64; a final
-// kernel adds the units of a tile in a fixed order and mirrors the upper triangle, so D is
-// exactly symmetric and reproducible run to run.
+// about 2^-44; each drain thread keeps hi of its 64 columns in registers and lo in tensor
+// memory for the whole work unit (tile, row range), and at its end writes hi + lo in FP64.  A final kernel
+// adds the units of a tile in a fixed order and mirrors the upper triangle, so D is exactly
+// symmetric and reproducible run to run.
 //
 // Kernel structure (one persistent CTA per SM, 320 threads):
 //   warp 0    TMA producer: H and L tiles of the a-block and of the b-block (128 snapshots x
-//             64 rows each, 128-byte swizzle) into a 3-stage shared ring;
+//             64 rows each, one contiguous 16 KB block of the tiled slice planes, 128-byte
+//             swizzle) into a 3-stage shared ring;
 //   warp 1    TMEM allocator and single-thread MMA issuer: tcgen05.mma M = 128, N = 128,
 //             K = 16 into one of two TMEM accumulators;
-//   warps 2-9 drain: tcgen05.ld of the finished accumulator, TwoSum into (hi, lo) in TMEM.
-// TMEM columns: [0, 128) and [128, 256) accumulators, [256, 384) hi, [384, 512) lo.
+//   warps 2-9 drain: tcgen05.ld of the finished accumulator, TwoSum into hi (registers) and
+//             lo (tensor memory).
+// TMEM columns: three 128-column accumulators (the MMA issuer runs two chunks ahead) and lo.
 // Work units are ordered split-major, so the CTAs running together read the same rows and
 // the slices come from HBM about once.  Every mbarrier wait is bounded in time; on expiry the
 // kernel records an error, lets its copies and MMAs finish (again with bounded waits), frees
@@ -45,13 +48,14 @@ constexpr size_t SMEM_BYTES = STAGES * (size_t)STAGE_BYTES + 1024;
 constexpr int NDRAIN = 8;
 constexpr int NTHREADS = 64 + 32 * NDRAIN;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t COL_HI = 256, COL_LO = 384;
+constexpr int NACC = 3;  // TMEM accumulators of 128 columns; the fourth block holds lo
+constexpr uint32_t COL_LO = 384;
 int64_t g_chunk_rows = 64;  // rows summed by one MMA accumulator before the TwoSum drain (tunable)
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kSmTarget = 152;  // the work split targets GB300's SM count, independent of the device queried
 
 struct TcShape {
-  int64_t n;
+  int64_t n, nrb;  // nrb: 64-row blocks of the tiled slice planes
   int k, tn, ntiles, splits, units;
   int64_t rows_per_split, chunk_rows;
 };
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                        double* __restrict__ part, unsigned* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], drain_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[NACC], acce_bar[NACC], drain_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NACC; ++b) {
       mbar_init(&accf_bar[b], 1);
       mbar_init(&acce_bar[b], NDRAIN);
     }
@@ -129,11 +133,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           uint8_t* base = smem + (size_t)stage * STAGE_BYTES;
           mbar_arrive_expect_tx(&full_bar[stage], STAGE_BYTES);
-          const int x = (int)row;
-          tma_load_2d(base, &mapH, &full_bar[stage], x, ta * BM);
-          tma_load_2d(base + TILE, &mapL, &full_bar[stage], x, ta * BM);
-          tma_load_2d(base + 2 * TILE, &mapH, &full_bar[stage], x, tb * BN);
-          tma_load_2d(base + 3 * TILE, &mapL, &full_bar[stage], x, tb * BN);
+          const int za = (int)(ta * sh.nrb + row / BK), zb = (int)(tb * sh.nrb + row / BK);
+          tma_load_3d(base, &mapH, &full_bar[stage], 0, 0, za);
+          tma_load_3d(base + TILE, &mapL, &full_bar[stage], 0, 0, za);
+          tma_load_3d(base + 2 * TILE, &mapH, &full_bar[stage], 0, 0, zb);
+          tma_load_3d(base + 3 * TILE, &mapL, &full_bar[stage], 0, 0, zb);
           stage = (stage + 1) % STAGES;
           ++it;
         }
@@ -153,8 +157,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int64_t k0 = (int64_t)(u / sh.ntiles) * sh.rows_per_split;
         const int64_t k1 = k0 + sh.rows_per_split < sh.n ? k0 + sh.rows_per_split : sh.n;
         for (int64_t c0 = k0; c0 < k1 && !abort_sh; c0 += sh.chunk_rows) {
-          const int buf = (int)(chunk & 1);
-          if (chunk >= 2 && !mbar_wait(&acce_bar[buf], (uint32_t)((chunk >> 1) - 1) & 1u, kWaitNs)) {
+          const int buf = (int)(chunk % NACC);
+          if (chunk >= NACC && !mbar_wait(&acce_bar[buf], (uint32_t)((chunk / NACC) - 1) & 1u, kWaitNs)) {
             fail(2u);
             break;
           }
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // --------------------------------------------------------------- drain (warps 2-9)
-    const int q = warp & 3;               // TMEM lane quadrant this warp may access
+    const int q = warp & 3;                  // TMEM lane quadrant this warp may access
     const int c0w = ((warp - 2) >> 2) * 64;  // this warp's 64 columns
     const int row = q * 32 + lane;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
@@ -209,10 +213,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int u = blockIdx.x; u < sh.units && !abort_sh; u += gridDim.x) {
       const int64_t k0 = (int64_t)(u / sh.ntiles) * sh.rows_per_split;
       const int64_t k1 = k0 + sh.rows_per_split < sh.n ? k0 + sh.rows_per_split : sh.n;
+      float hi[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) hi[j] = 0.f;
       bool ok = true;
       for (int64_t c0 = k0; c0 < k1; c0 += sh.chunk_rows) {
-        const int buf = (int)(chunk & 1);
-        ok = mbar_wait(&accf_bar[buf], (uint32_t)(chunk >> 1) & 1u, kWaitNs);
+        const int buf = (int)(chunk % NACC);
+        ok = mbar_wait(&accf_bar[buf], (uint32_t)(chunk / NACC) & 1u, kWaitNs);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) {
           if (lane == 0) fail(8u);
@@ -220,53 +227,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc_fence_after();
         const bool first = c0 == k0;
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
-          const uint32_t col = (uint32_t)(c0w + g * 32);
-          uint32_t a[32], hi[32], lo[32];
-          tmem_ld_32x32b_x32(tmem + lane_off + (uint32_t)(buf * BN) + col, a);
-          if (!first) {
-            tmem_ld_32x32b_x32(tmem + lane_off + COL_HI + col, hi);
-            tmem_ld_32x32b_x32(tmem + lane_off + COL_LO + col, lo);
-          }
+        // a 16-column quarter at a time: hi in registers, lo in tensor memory
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const uint32_t col = (uint32_t)(c0w + g * 16);
+          uint32_t a[16], lo[16];
+          tmem_ld_32x32b_x16(tmem + lane_off + (uint32_t)(buf * BN) + col, a);
+          if (!first) tmem_ld_32x32b_x16(tmem + lane_off + COL_LO + col, lo);
           tmem_wait_ld();
-          if (first) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              hi[j] = a[j];
-              lo[j] = 0u;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              float e;
-              const float s = two_sum_hi(__uint_as_float(hi[j]), __uint_as_float(a[j]), e);
-              hi[j] = __float_as_uint(s);
-              lo[j] = __float_as_uint(__fadd_rn(__uint_as_float(lo[j]), e));
-            }
+          if (g == 3) {  // the accumulator is free once all quarters are loaded
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[buf]);
           }
-          tmem_st_32x32b_x32(tmem + lane_off + COL_HI + col, hi);
-          tmem_st_32x32b_x32(tmem + lane_off + COL_LO + col, lo);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float e;
+            hi[g * 16 + j] = two_sum_hi(hi[g * 16 + j], __uint_as_float(a[j]), e);
+            lo[j] = first ? __float_as_uint(e) : __float_as_uint(__fadd_rn(__uint_as_float(lo[j]), e));
+          }
+          tmem_st_32x32b_x16(tmem + lane_off + COL_LO + col, lo);
         }
         tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acce_bar[buf]);
         ++chunk;
       }
       if (!ok) break;
       // unit finished: hi + lo of this warp's columns, in FP64, to the unit's partial tile
       double* P = part + (size_t)u * BM * BN;
-#pragma unroll 1
+#pragma unroll
       for (int g = 0; g < 2; ++g) {
-        const uint32_t col = (uint32_t)(c0w + g * 32);
-        uint32_t hi[32], lo[32];
-        tmem_ld_32x32b_x32(tmem + lane_off + COL_HI + col, hi);
-        tmem_ld_32x32b_x32(tmem + lane_off + COL_LO + col, lo);
+        uint32_t lo[32];
+        tmem_ld_32x32b_x32(tmem + lane_off + COL_LO + (uint32_t)(c0w + g * 32), lo);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          P[(size_t)(col + j) * BM + row] = (double)__uint_as_float(hi[j]) + (double)__uint_as_float(lo[j]);
+          P[(size_t)(c0w + g * 32 + j) * BM + row] = (double)hi[g * 32 + j] + (double)__uint_as_float(lo[j]);
       }
     }
   }
@@ -294,24 +289,31 @@ __global__ void gram_tc_reduce(const double* __restrict__ part, TcShape sh, int 
   D[b + (int64_t)a * ldd] = s;
 }
 
-// h = bf16(x), l = bf16(x - h), planes with leading dimension lds.
+// h = bf16(x), l = bf16(x - h) in the tiled slice layout: the plane is a sequence of
+// 64-row x 128-column blocks, block (column block cb, row block rb) at index cb * nrb + rb,
+// each 16 KB contiguous with its 128 columns one after the other (64 rows = 128 bytes each).
+// One TMA box is then one contiguous read.  Rows >= n and columns >= k are written as zeros.
 template <typename T>
 __global__ void split_bf16(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq, __nv_bfloat16* __restrict__ H,
-                           __nv_bfloat16* __restrict__ L, int64_t lds) {
-  const int64_t total = n * k;
+                           __nv_bfloat16* __restrict__ L, int64_t nrb, int64_t ncb) {
+  const int64_t rows = nrb * BK, cols = ncb * BM;
+  const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % n, t = e / n;
-    const T x = Q[i + t * ldq];
-    __nv_bfloat16 h, l;
-    if constexpr (sizeof(T) == 8) {
-      h = __double2bfloat16(x);
-      l = __double2bfloat16(x - (double)__bfloat162float(h));
-    } else {
-      h = __float2bfloat16_rn(x);
-      l = __float2bfloat16_rn(x - __bfloat162float(h));
+    const int64_t i = e % rows, t = e / rows;
+    __nv_bfloat16 h = __float2bfloat16_rn(0.0f), l = h;
+    if (i < n && t < k) {
+      const T x = Q[i + t * ldq];
+      if constexpr (sizeof(T) == 8) {
+        h = __double2bfloat16(x);
+        l = __double2bfloat16(x - (double)__bfloat162float(h));
+      } else {
+        h = __float2bfloat16_rn(x);
+        l = __float2bfloat16_rn(x - __bfloat162float(h));
+      }
     }
-    H[i + t * lds] = h;
-    L[i + t * lds] = l;
+    const int64_t off = ((t / BM) * nrb + i / BK) * (BM * BK) + (t % BM) * BK + (i % BK);
+    H[off] = h;
+    L[off] = l;
   }
 }
 
@@ -319,6 +321,7 @@ TcShape make_shape(int64_t n, int64_t k) {
   const int sms = kSmTarget;
   TcShape s;
   s.n = n;
+  s.nrb = (n + BK - 1) / BK;
   s.k = (int)k;
   s.tn = (int)((k + BM - 1) / BM);
   s.ntiles = s.tn * (s.tn + 1) / 2;
@@ -373,16 +376,16 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over a BF16 plane (inner dimension n rows, outer k columns, leading dimension
-// lds elements), box of 64 rows x 128 columns, 128-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap* map, void* base, int64_t n, int64_t k, int64_t lds) {
+// 3-D map over a tiled BF16 plane: (64 rows, 128 columns, blocks), box = one block, 128-byte
+// swizzle.  The box lands in shared memory as 128 rows (columns of Q) of 128 bytes.
+bool make_map(CUtensorMap* map, void* base, int64_t nblocks) {
   EncodeTiledFn f = encode_fn();
   if (!f) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
-  cuuint64_t strides[1] = {(cuuint64_t)(lds * 2)};
-  cuuint32_t box[2] = {BK, BM};
-  cuuint32_t estr[2] = {1, 1};
-  return f(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  cuuint64_t dims[3] = {(cuuint64_t)BK, (cuuint64_t)BM, (cuuint64_t)nblocks};
+  cuuint64_t strides[2] = {(cuuint64_t)(BK * 2), (cuuint64_t)(BK * BM * 2)};
+  cuuint32_t box[3] = {BK, BM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return f(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -391,7 +394,7 @@ struct TcWs {
   __nv_bfloat16 *H, *L;
   double* part;
   unsigned* err;
-  int64_t lds;
+  int64_t nrb, ncb;
   size_t used;
 };
 
@@ -399,9 +402,10 @@ TcWs carve_tc(void* base, int64_t n, int64_t k) {
   const TcShape s = make_shape(n, k);
   Carver c(base);
   TcWs w;
-  w.lds = (n + 63) / 64 * 64;
-  w.H = c.take<__nv_bfloat16>((size_t)w.lds * k);
-  w.L = c.take<__nv_bfloat16>((size_t)w.lds * k);
+  w.nrb = (n + BK - 1) / BK;
+  w.ncb = (k + BM - 1) / BM;
+  w.H = c.take<__nv_bfloat16>((size_t)w.nrb * w.ncb * BK * BM);
+  w.L = c.take<__nv_bfloat16>((size_t)w.nrb * w.ncb * BK * BM);
   w.part = c.take<double>((size_t)s.units * BM * BN);
   w.err = c.take<unsigned>(1);
   w.used = c.used;
@@ -421,20 +425,29 @@ int64_t gram_tc_set_chunk_rows(int64_t rows) {
 int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
             void* ws, size_t ws_bytes, cudaStream_t st) {
   if (n > ((int64_t)1 << 31) - BK || k > 65535) return DOPINF_E_UNSUPPORTED;
+  if (((n + BK - 1) / BK) * ((k + BM - 1) / BM) > (int64_t)INT32_MAX) return DOPINF_E_UNSUPPORTED;
   if (!ws || ws_bytes < gram_tc_workspace(n, k) || misaligned(ws)) return DOPINF_E_ARG;
   TcWs w = carve_tc(ws, n, k);
   const TcShape sh = make_shape(n, k);
-  const int64_t total = n * k;
+  const int64_t total = w.nrb * BK * w.ncb * BM;
   const unsigned sblocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
   if (dtype == DOPINF_F64)
-    split_bf16<double><<<sblocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.H, w.L, w.lds);
+    split_bf16<double><<<sblocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.H, w.L, w.nrb, w.ncb);
   else
-    split_bf16<float><<<sblocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.H, w.L, w.lds);
+    split_bf16<float><<<sblocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.H, w.L, w.nrb, w.ncb);
   DOPINF_TRY(launch_status());
   CUtensorMap mh, ml;
-  if (!make_map(&mh, w.H, n, k, w.lds) || !make_map(&ml, w.L, n, k, w.lds)) return DOPINF_E_CUDA;
+  if (!make_map(&mh, w.H, w.nrb * w.ncb) || !make_map(&ml, w.L, w.nrb * w.ncb)) return DOPINF_E_CUDA;
   DOPINF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(unsigned), st));
   DOPINF_CUDA(cudaFuncSetAttribute(gram_bf16x4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+  {
+    int per_sm = 0;  // the kernel needs one resident CTA per SM (registers, shared memory)
+    DOPINF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_bf16x4_kernel, NTHREADS, SMEM_BYTES));
+    if (per_sm < 1) {
+      set_last_error("gram_bf16x4_kernel does not fit on an SM", cudaErrorLaunchOutOfResources);
+      return DOPINF_E_CUDA;
+    }
+  }
   const int grid = sh.units < num_sms() ? sh.units : num_sms();
   gram_bf16x4_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(mh, ml, sh, w.part, w.err);
   DOPINF_TRY(launch_status());

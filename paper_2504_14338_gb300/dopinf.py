@@ -21,7 +21,7 @@ OK, E_ARG, E_CUDA, E_NONFINITE, E_RANK, E_NO_STABLE, E_TIMEOUT, E_UNSUPPORTED = 
 FLAG_NONFINITE, FLAG_ZERO_SCALE = 1, 2
 F64, F32 = 0, 1
 CENTER, SCALE = 1, 2
-GRAM_FP64, GRAM_BF16X4 = 0, 1
+GRAM_FP64, GRAM_BF16X4, GRAM_OZAKI_FP64 = 0, 1, 2
 DISCRETE, CONTINUOUS_RK4 = 0, 1
 
 _c_i64 = ctypes.c_int64
@@ -32,7 +32,9 @@ _c_sz = ctypes.c_size_t
 class DopinfError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
-        super().__init__("%s failed: %d (%s)" % (fn, status, status_string(status)))
+        detail = lib.dopinf_last_error().decode() if status == E_CUDA else ""
+        super().__init__("%s failed: %d (%s)%s" % (fn, status, status_string(status),
+                                                    " - " + detail if detail else ""))
 
 
 def _load():
@@ -42,6 +44,7 @@ def _load():
     lib = ctypes.CDLL(LIB_PATH)
     sig = {
         "dopinf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "dopinf_last_error": (ctypes.c_char_p, []),
         "dopinf_transform_workspace": (_c_sz, [_c_i64, ctypes.c_int]),
         "dopinf_transform": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int,
                                             ctypes.POINTER(_c_i64), ctypes.c_uint, _c_p, _c_p, _c_p,
@@ -65,6 +68,14 @@ def _load():
         "dopinf_tune_learn_cluster": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_rollout": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_p, _c_i64, ctypes.c_int,
                                           ctypes.c_double, _c_p, _c_p, _c_p]),
+        "dopinf_proposal_features": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.c_double, _c_p, ctypes.c_int,
+                                                    _c_i64, _c_i64, _c_p, _c_p]),
+        "dopinf_mlp_param_count": (_c_sz, [ctypes.c_int]),
+        "dopinf_mlp_workspace": (_c_sz, [ctypes.c_int, ctypes.c_int]),
+        "dopinf_mlp_forward": (ctypes.c_int, [_c_p, ctypes.c_int, _c_p, ctypes.c_int, _c_p, _c_p, _c_sz, _c_p]),
+        "dopinf_mlp_train_step": (ctypes.c_int, [_c_p, _c_p, _c_p, ctypes.c_int, ctypes.c_float,
+                                                 ctypes.POINTER(ctypes.c_int), _c_p, _c_p, ctypes.c_int, _c_p, _c_p,
+                                                 _c_p, _c_sz, _c_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -246,3 +257,43 @@ def dopinf_rollout(O, q0, n_steps, mode=DISCRETE, dt=1.0, stream=None):
     _check("dopinf_rollout", lib.dopinf_rollout(_ptr(O), r, O.stride(1) if d > 1 else r, _ptr(q0), int(n_steps),
                                                 int(mode), float(dt), _ptr(Qt), _ptr(fin), _stream(stream)))
     return Qt, fin
+
+
+# ------------------------------------------------------------------------------ proposal network
+def dopinf_proposal_features(eigvals, trace, Qhat, stream=None):
+    """64 FP32 features (device tensor) of a reduced system."""
+    r_max, k = Qhat.shape
+    f = torch.empty(64, dtype=torch.float32, device=Qhat.device)
+    eig = eigvals.contiguous()
+    _check("dopinf_proposal_features", lib.dopinf_proposal_features(_ptr(eig), eig.numel(), float(trace), _ptr(Qhat),
+                                                                    r_max, k, Qhat.stride(1), _ptr(f), _stream(stream)))
+    return f
+
+
+def dopinf_mlp_param_count(n_out):
+    return int(lib.dopinf_mlp_param_count(int(n_out)))
+
+
+def dopinf_mlp_forward(params, n_out, X, ws=None, stream=None):
+    B = X.shape[0]
+    logits = torch.empty(B, n_out, dtype=torch.float32, device=X.device)
+    nb = lib.dopinf_mlp_workspace(B, n_out)
+    buf, nb = _ws(nb, ws, X.device)
+    _check("dopinf_mlp_forward", lib.dopinf_mlp_forward(_ptr(params), n_out, _ptr(X.contiguous()), B, _ptr(logits),
+                                                        _ptr(buf), nb, _stream(stream)))
+    return logits
+
+
+def dopinf_mlp_train_step(params, m, v, step, lr, head_sizes, X, labels, want_grad=False, ws=None, stream=None):
+    """One forward/backward/Adam step in place on params, m, v; returns (loss tensor, grad or None)."""
+    B = X.shape[0]
+    n_out = sum(head_sizes)
+    hs = (ctypes.c_int * 3)(*[int(h) for h in head_sizes])
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    grad = torch.empty(dopinf_mlp_param_count(n_out), dtype=torch.float32, device=X.device) if want_grad else None
+    nb = lib.dopinf_mlp_workspace(B, n_out)
+    buf, nb = _ws(nb, ws, X.device)
+    _check("dopinf_mlp_train_step", lib.dopinf_mlp_train_step(_ptr(params), _ptr(m), _ptr(v), int(step), float(lr), hs,
+                                                              _ptr(X.contiguous()), _ptr(labels.contiguous()), B,
+                                                              _ptr(loss), _ptr(grad), _ptr(buf), nb, _stream(stream)))
+    return loss, grad

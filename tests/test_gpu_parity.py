@@ -156,6 +156,32 @@ def test_gram_bf16x4_eigenvalues_within_target(dp):
     assert err <= 1e-6
 
 
+@pytest.mark.parametrize("n,k,dtype", [(100_003, 300, "f64"), (4096, 200, "f64"), (20_011, 129, "f32"), (70, 17, "f64")])
+def test_gram_ozaki_fp64_vs_oracle(dp, n, k, dtype):
+    # exact digit products: the only errors are the 2^-57 digit truncation (relative to the
+    # column max) and the FP64 sums of the partials, far inside the FP64 path's bound
+    rng = np.random.default_rng(n + 3 * k)
+    Qn = rng.standard_normal((n, k)) * np.exp(rng.uniform(-3, 3, k)) * np.exp(rng.uniform(-2, 2, (n, 1)))
+    if dtype == "f32":
+        Qn = Qn.astype(np.float32)
+    Q = to_dev(dp, Qn)
+    D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64).cpu().numpy()
+    ref = O.gram(Qn)
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    rel = np.abs(D - ref) / scale
+    print("ozaki max rel", rel.max())
+    assert np.all(np.abs(D - ref) <= 4 * np.sqrt(n) * EPS * scale)
+    assert np.array_equal(D, D.T)
+
+
+def test_gram_ozaki_exact_on_integers(dp):
+    # small integers have exact digits and exact FP64 sums: D must equal Q^T Q exactly
+    rng = np.random.default_rng(9)
+    Qn = rng.integers(-1000, 1001, (30_000, 96)).astype(np.float64)
+    D = dp.dopinf_gram(to_dev(dp, Qn), mode=dp.GRAM_OZAKI_FP64).cpu().numpy()
+    assert np.array_equal(D, O.gram(Qn))
+
+
 # ------------------------------------------------------------------------------ Step III reduce
 def _pipeline_D(seed=1234, n_vars=2, n_per=2048, k=200, r_true=6, scales=()):
     w = synth.Workload("t", n_vars, n_per, k, r_true, var_scales=scales, seed=seed)
