@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--n-per-var", type=int, default=0, help="override rows per variable (smaller case)")
     p.add_argument("--no-split", action="store_true", help="skip the split-precision Gram measurement")
     p.add_argument("--gram-mode", default="fp64", choices=["fp64", "bf16x4", "ozaki"], help="Gram mode of --stage gram")
+    p.add_argument("--pipeline-gram", default="ozaki", choices=["fp64", "ozaki"],
+                   help="FP64-accurate Gram of the pipeline: FP64 pipe, or exact digit products on the tensor cores")
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential grid-search baseline")
     return p.parse_args()
 
@@ -59,7 +61,7 @@ def config_of(w):
         w.name, w.n_vars, w.n_per_var, w.n, w.k, w.r_true, list(w.r_list), w.n_beta1, w.n_beta2, w.n_steps,
         "RK4" if w.mode == "continuous" else "discrete", w.dtype),
         "n": w.n, "k": w.k, "r_list": list(w.r_list), "grid": [w.n_beta1, w.n_beta2], "n_steps": w.n_steps,
-        "gram_mode": "fp64", "l2": "inputs larger than L2 (%.2f GB snapshot matrix)" % (w.n * w.k * 8 / 1e9)}
+        "l2": "inputs larger than L2 (%.2f GB snapshot matrix)" % (w.n * w.k * 8 / 1e9)}
 
 
 # ------------------------------------------------------------------------------------ clocks
@@ -229,6 +231,40 @@ def split_gram_measure(dp, synth, dev, frac=16):
             "transform_gbs": 3 * w.n * w.k * 4 / t_transform / 1e6}
 
 
+def gram_modes_measure(dp, Q, D_pipe, pipe_name, pipe_ms, ws):
+    """The three Gram modes on the pipeline's (transformed) snapshot matrix: time of the FP64
+    pipe and of the split BF16x4 Gram, and each one's largest deviation from the FP64 pipe's D
+    relative to sqrt(D_aa D_bb)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    n, k = Q.shape
+
+    def timed(mode, reps):
+        D = dp.dopinf_gram(Q, mode=mode, ws=ws)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dp.dopinf_gram(Q, mode=mode, D=D, ws=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return D, float(np.mean(ts))
+
+    D64, t64 = timed(dp.GRAM_FP64, 1)
+    D16, t16 = timed(dp.GRAM_BF16X4, 2)
+    d = torch.sqrt(torch.diagonal(D64).abs())
+    sc = torch.outer(d, d)
+
+    def dev(D):
+        return float(((D - D64).abs() / sc).max())
+    useful = n * k * (k + 1)
+    return {"fp64_pipe_ms": t64, "fp64_pipe_useful_tflops": useful / t64 / 1e9,
+            "%s_ms" % pipe_name: pipe_ms, "%s_max_rel_vs_fp64_pipe" % pipe_name: dev(D_pipe),
+            "bf16x4_ms": t16, "bf16x4_max_rel_vs_fp64_pipe": dev(D16),
+            "speedup_%s_vs_fp64_pipe" % pipe_name: t64 / pipe_ms}
+
+
 def sequential_learn_measure(dp, Qhat, w, mode):
     """The grid search one candidate at a time (one dopinf_learn call per (r, beta1, beta2),
     one CTA per rollout): the unbatched baseline of the batched learn step."""
@@ -318,12 +354,15 @@ def main():
 
     last = {}
 
+    pipe_mode = dp.GRAM_OZAKI_FP64 if args.pipeline_gram == "ozaki" else dp.GRAM_FP64
+
     def step(record=False):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         e[0].record(stream)
         dp.dopinf_transform(Q, offs, ws=ws)
         e[1].record(stream)
-        D = dp.dopinf_gram(Q, ws=ws)
+        D = dp.dopinf_gram(Q, mode=pipe_mode, ws=ws)
+        last["D"] = D
         e[2].record(stream)
         red = dp.dopinf_reduce(D, r_cap=r_max, r_fixed=r_max, ws=ws)
         last["red"] = red
@@ -364,6 +403,7 @@ def main():
     stage = {nm: float(np.mean([es[i].elapsed_time(es[i + 1]) for es in ev["stages"]])) for i, nm in enumerate(names)}
     gram_flops = w.n * w.k * (w.k + 1)
     gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
+    modes = gram_modes_measure(dp, Q, last["D"], args.pipeline_gram, stage["gram"], ws) if rank == 0 else None
 
     # e2e: host snapshot matrix (pinned) -> device, the pipeline through the C ABI, results back
     e2e = None
@@ -393,12 +433,25 @@ def main():
         pass
     bf16 = peaks.get("bf16_tflops") or 1900.0
     fp64_peak = bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
-    roof = {"kernel": "tn_partial (FP64 Gram, split-K) + tn_reduce", "bound": "alu", "achieved": gram_tf * 1e3,
-            "peak": fp64_peak * 1e3, "unit": "GFLOP/s", "frac": gram_tf / fp64_peak,
-            "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)",
-            "traffic": None, "algorithmic_flops_per_launch": gram_flops}
+    if args.pipeline_gram == "ozaki":
+        # the digit products the kernel must execute for an FP64-exact D: 36 BF16 products over the
+        # 128 x 128 upper tiles of every 64-row block
+        tn = (w.k + 127) // 128
+        executed = 36 * 2 * 128 * 128 * ((w.n + 63) // 64 * 64) * (tn * (tn + 1) // 2)
+        ach = executed / (stage["gram"] / 1e3) / 1e12
+        roof = {"kernel": "ozaki_pass_kernel x 8 + colmax/digits/reduce (FP64-accurate Gram)", "bound": "tensor",
+                "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                "peak_source": "measured bf16 burst (of measured)", "traffic": None,
+                "algorithmic_flops_per_launch": executed,
+                "fp64_equivalent_tflops": gram_tf, "fp64_equivalent_vs_fp64_peak": gram_tf / fp64_peak}
+    else:
+        roof = {"kernel": "tn_partial (FP64 Gram, split-K) + tn_reduce", "bound": "alu", "achieved": gram_tf * 1e3,
+                "peak": fp64_peak * 1e3, "unit": "GFLOP/s", "frac": gram_tf / fp64_peak,
+                "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)",
+                "traffic": None, "algorithmic_flops_per_launch": gram_flops}
     k = w.k
-    launches = 3 + 2 + (3 * (k - 2) + 8) + (8 * len(w.r_list) + 1)
+    gram_launches = 11 if args.pipeline_gram == "ozaki" else 2
+    launches = 3 + gram_launches + (3 * (k - 2) + 8) + (6 * len(w.r_list) + 3)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         per, desc, wall = oracle_sample(w)
@@ -418,7 +471,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
-                "stages_ms": stage, "gram_tflops_fp64": gram_tf, "learn_s": stage["learn"] / 1e3,
+                "stages_ms": stage, "pipeline_gram": args.pipeline_gram, "gram_useful_tflops": gram_tf,
+                "gram_modes": modes, "learn_s": stage["learn"] / 1e3,
                 "best": {"index": best, "r": res.get("r"), "beta1": res.get("beta1"), "beta2": res.get("beta2")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "split_gram": split, "learn_vs_sequential": seq}

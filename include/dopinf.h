@@ -175,6 +175,12 @@ size_t dopinf_reduce_workspace(int64_t k, int r_cap);
 int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed,
                   int r_cap, int* r_out, double* trace_out, double* eigvals, double* Tr,
                   double* Qhat, void* ws, size_t ws_bytes, void* stream);
+/* Tuning of dopinf_reduce: 1 (default) reduces D to tridiagonal form in one cooperative
+ * launch with a grid barrier per column (where 3 k doubles of shared memory fit, k <= 8533,
+ * and the device supports cooperative launches); 0 uses three launches per column.  Both
+ * give the same bits.  If the grid barrier waits longer than 2 s, dopinf_reduce returns
+ * DOPINF_E_TIMEOUT.  Other values only query.  Returns the previous value.  Process-wide. */
+int dopinf_tune_reduce_coop(int on);
 
 /* ------------------------------------------------------------------------------------
  * Step IV: quadratic OpInf with the (r, beta1, beta2) grid search (eqs. OpInf_reg,

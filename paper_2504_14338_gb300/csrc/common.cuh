@@ -83,6 +83,26 @@ int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int acc
 // ---------------------------------------------------------------------------------------
 // Batched ROM rollouts (rollout.cu): one thread-block cluster per candidate.
 // ---------------------------------------------------------------------------------------
+// Block-Schur solve of the regularised normal equations of all candidates (schur.cu).
+struct SchurUnit {  // one (r, beta2)
+  const double* G;  // d x d normal matrix of this r (ld d)
+  const double* B;  // d x r right-hand sides (ld d)
+  double* E;        // N x N (ld N) working matrix, N = s + m + r
+  double b2;
+  int r, d, s, m, N, unit;
+};
+struct SchurCand {  // one (r, beta1, beta2)
+  const double* E;  // its unit's working matrix
+  double* O;        // r x d operator output (ld r)
+  double* scratch;  // schur_cand_doubles(r) doubles
+  double b1;
+  int r, s, m, N, unit, cand;
+};
+size_t schur_unit_doubles(int r);
+size_t schur_cand_doubles(int r);
+int schur_solve(const SchurUnit* units_dev, const SchurUnit* units_host, int n_units, const SchurCand* cands_dev,
+                int n_cand, int* unit_fail, int* cand_status, cudaStream_t st);
+
 struct RolloutCand {
   const double* O;      // r x d column-major operator [A | H | c], leading dimension ldo
   int64_t ldo;

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(EB) hh_rank2(double* A, int64_t k, int64_t j, 
     double* col = A + (j + 1 + c) * k + (j + 1);
     for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
       const double wr = fma(alpha, v[r], p[r]);
-      col[r] = col[r] - v[r] * wc - wr * vc;
+      col[r] = fma(-wr, vc, fma(-v[r], wc, col[r]));
     }
   }
 }
@@ -119,6 +119,177 @@ __global__ void hh_tail(const double* A, int64_t k, double* d, double* e, double
   d[k - 1] = A[(k - 1) * k + (k - 1)];
   e[k - 1] = 0.0;
   tau[k - 1] = 0.0;
+}
+
+// ---------------------------------------------------------------------------------------
+// The same reduction in one cooperative launch.  The rank-2 update of step j is applied by
+// the warp that also forms row c of the next product p_{j+1} = tau_{j+1} A22 v_{j+1} (the
+// matrix is symmetric, so row c is column c): each trailing column is read and written once
+// per step, and one grid barrier per column separates the steps.  Every CTA forms the next
+// reflector redundantly from its own copy of the updated column j+1, with the reductions in
+// the same fixed order as the three-launch version, so the results agree bit for bit.
+// The barrier is a counter and a generation word with a bounded wait: on expiry the kernel
+// sets an error word and every CTA returns.
+constexpr int TB = 256;
+constexpr uint64_t kBarNs = 2000000000ull;
+struct GridBar {
+  unsigned count, gen, err;
+};
+
+__device__ __forceinline__ uint64_t gtimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_sync(GridBar* b) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &b->gen;
+    volatile unsigned* verr = &b->err;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const uint64_t t0 = gtimer_ns();
+      while (*vgen == g) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (gtimer_ns() - t0 > kBarNs) {
+          atomicOr(&b->err, 1u);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Householder vector of the column held in x (absolute rows, entries j+1..k-1), in place:
+// x[j+1] = 1, x[j+2..] scaled; returns tau, beta through the references (as hh_gen).
+__device__ void reflector_inplace(double* x, int64_t k, int64_t j, double* sh, double& t, double& beta) {
+  double part = 0.0;
+  for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) part += x[i] * x[i];
+  const double sigma2 = block_sum(part, sh);
+  const double x0 = x[j + 1];
+  double scal;
+  if (sigma2 == 0.0) {
+    t = 0.0;
+    beta = x0;
+    scal = 0.0;
+  } else {
+    const double nrm = sqrt(x0 * x0 + sigma2);
+    beta = x0 >= 0.0 ? -nrm : nrm;
+    t = (beta - x0) / beta;
+    scal = 1.0 / (x0 - beta);
+  }
+  __syncthreads();
+  if (t != 0.0)
+    for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) x[i] *= scal;
+  __syncthreads();
+  if (threadIdx.x == 0) x[j + 1] = 1.0;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, double* d, double* e, double* tau,
+                                                      double* pg, GridBar* bar) {
+  extern __shared__ double smd[];
+  double* vj = smd;          // v_j (rows j+1..k-1)
+  double* pj = smd + k;      // p_j
+  double* vn = smd + 2 * k;  // column j+1 after update j, then v_{j+1}
+  __shared__ double sh[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (TB / 32) + warp, nw = (int64_t)gridDim.x * (TB / 32);
+  double tj = 0.0;  // tau of the pending update (0: none)
+  for (int64_t j = -1; j + 2 < k; ++j) {
+    // (a) the pending update of step j: alpha = -tau_j/2 (p_j . v_j), w = p + alpha v
+    double alpha = 0.0;
+    if (j >= 0 && tj != 0.0) {
+      const int64_t m = k - j - 1;
+      double part = 0.0;
+      for (int64_t l = threadIdx.x; l < m; l += blockDim.x) part = fma(pj[j + 1 + l], vj[j + 1 + l], part);
+      alpha = -0.5 * tj * block_sum(part, sh);
+    }
+    const bool upd = j >= 0 && tj != 0.0;
+    // (b) column j+1 after update j, rows j+1..k-1
+    const int64_t c1 = j + 1;
+    {
+      const double vc = upd ? vj[c1] : 0.0, wc = upd ? fma(alpha, vc, pj[c1]) : 0.0;
+      for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) {
+        double a = __ldcg(A + r + c1 * k);
+        if (upd) {
+          const double wr = fma(alpha, vj[r], pj[r]);
+          a = fma(-wr, vc, fma(-vj[r], wc, a));
+        }
+        vn[r] = a;
+      }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) d[c1] = vn[c1];
+    // (c) the stored reflector of column j (nobody reads column j any more)
+    if (blockIdx.x == 0 && j >= 0) {
+      for (int64_t r = j + 1 + threadIdx.x; r < k; r += blockDim.x) A[r + j * k] = vj[r];
+    }
+    if (c1 + 2 >= k) {
+      // last step: the trailing 2 x 2 block
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        e[c1] = vn[c1 + 1];
+        tau[c1] = 0.0;
+        const int64_t r = k - 1;
+        double a = __ldcg(A + r + r * k);
+        if (upd) {
+          const double vc = vj[r], wc = fma(alpha, vc, pj[r]);
+          a = fma(-wc, vc, fma(-vj[r], wc, a));
+        }
+        d[r] = a;
+        e[r] = 0.0;
+        tau[r] = 0.0;
+      }
+      return;
+    }
+    double tn, beta;
+    reflector_inplace(vn, k, c1, sh, tn, beta);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      e[c1] = beta;
+      tau[c1] = tn;
+    }
+    // (d) update j on the trailing columns c >= j+2 (rows >= j+2), fused with p_{j+1}[c]
+    if (tn != 0.0 || upd) {
+      const int64_t r0 = c1 + 1;
+      // column c belongs to warp c mod nw for the whole reduction
+      for (int64_t c = r0 + ((gw - r0) % nw + nw) % nw; c < k; c += nw) {
+        double* col = A + c * k;
+        const double vc = upd ? vj[c] : 0.0, wc = upd ? fma(alpha, vc, pj[c]) : 0.0;
+        double s = 0.0;
+        for (int64_t l = lane; l < k - r0; l += 32) {
+          const int64_t r = r0 + l;
+          double a = __ldcg(col + r);
+          if (upd) {
+            const double wr = fma(alpha, vj[r], pj[r]);
+            a = fma(-wr, vc, fma(-vj[r], wc, a));
+            col[r] = a;
+          }
+          s = fma(a, vn[r], s);
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) pg[c] = tn * s;
+      }
+    }
+    if (!grid_sync(bar)) return;
+    // (e) p_{j+1} to shared memory, v_{j+1} becomes the pending reflector
+    for (int64_t r = c1 + 1 + threadIdx.x; r < k; r += blockDim.x) pj[r] = tn != 0.0 ? __ldcg(pg + r) : 0.0;
+    for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) vj[r] = vn[r];
+    tj = tn;
+    __syncthreads();
+  }
 }
 
 // Gershgorin interval and the pivot floor of the Sturm count.
@@ -370,6 +541,7 @@ struct ReduceWs {
   double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *Dg, *Du, *Du2, *Dl, *trace;
   unsigned char* piv;
   int* r;
+  GridBar* bar;
   void* tn;
   size_t tn_bytes, used;
 };
@@ -387,6 +559,7 @@ ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
   w.tnorm = c.take<double>(1);
   w.trace = c.take<double>(1);
   w.r = c.take<int>(1);
+  w.bar = c.take<GridBar>(1);
   w.Z = c.take<double>((size_t)k * r_cap);
   w.U = c.take<double>((size_t)k * r_cap);
   w.Dg = c.take<double>((size_t)k * r_cap);
@@ -400,10 +573,55 @@ ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
   return w;
 }
 
+// Householder tridiagonalisation of w.A: one cooperative launch (grid barrier per column)
+// where 3 k doubles of shared memory fit, else three launches per column.
+int g_reduce_coop = 1;
+
+int tridiagonalise(const ReduceWs& w, int64_t k, cudaStream_t st) {
+  const size_t smem = (size_t)3 * k * sizeof(double);
+  DOPINF_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), st));
+  int dev = 0, sms = 0, coop = 0;
+  DOPINF_CUDA(cudaGetDevice(&dev));
+  DOPINF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DOPINF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (g_reduce_coop && k >= 3 && coop && smem <= 200 * 1024) {
+    DOPINF_CUDA(cudaFuncSetAttribute(hh_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    DOPINF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_tridiag_coop, TB, smem));
+    if (per_sm >= 1) {
+      // about one warp per trailing column, at most one CTA per SM (a cheap barrier)
+      int64_t grid = (k - 1 + (TB / 32) - 1) / (TB / 32);
+      if (grid > sms) grid = sms;
+      if (grid < 1) grid = 1;
+      double* A = w.A;
+      double *d = w.d, *e = w.e, *tau = w.tau, *p = w.p;
+      GridBar* bar = w.bar;
+      int64_t kk = k;
+      void* args[] = {&A, &kk, &d, &e, &tau, &p, &bar};
+      DOPINF_CUDA(cudaLaunchCooperativeKernel((const void*)hh_tridiag_coop, dim3((unsigned)grid), dim3(TB), args, smem, st));
+      return launch_status();  // the barrier's error word is read with the results
+    }
+  }
+  for (int64_t j = 0; j + 2 < k; ++j) {
+    const int64_t m = k - j - 1;
+    hh_gen<<<1, EB, 0, st>>>(w.A, k, j, w.d, w.e, w.tau);
+    hh_symv<<<(unsigned)((m + 7) / 8), EB, 0, st>>>(w.A, k, j, w.tau, w.p);
+    hh_rank2<<<(unsigned)((m + R2_COLS - 1) / R2_COLS), EB, 0, st>>>(w.A, k, j, w.tau, w.p);
+  }
+  hh_tail<<<1, 32, 0, st>>>(w.A, k, w.d, w.e, w.tau);
+  return launch_status();
+}
+
 }  // namespace
 }  // namespace dopinf
 
 using namespace dopinf;
+
+DOPINF_API int dopinf_tune_reduce_coop(int on) {
+  const int prev = g_reduce_coop;
+  if (on == 0 || on == 1) g_reduce_coop = on;
+  return prev;
+}
 
 DOPINF_API size_t dopinf_reduce_workspace(int64_t k, int r_cap) {
   if (k < 1 || r_cap < 1) return 0;
@@ -423,14 +641,7 @@ DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double ene
   ReduceWs w = carve_reduce(ws, k, r_cap);
   DOPINF_CUDA(cudaMemcpy2DAsync(w.A, k * sizeof(double), D, ldd * sizeof(double), k * sizeof(double), k,
                                 cudaMemcpyDeviceToDevice, st));
-  for (int64_t j = 0; j + 2 < k; ++j) {
-    const int64_t m = k - j - 1;
-    hh_gen<<<1, EB, 0, st>>>(w.A, k, j, w.d, w.e, w.tau);
-    hh_symv<<<(unsigned)((m + 7) / 8), EB, 0, st>>>(w.A, k, j, w.tau, w.p);
-    hh_rank2<<<(unsigned)((m + R2_COLS - 1) / R2_COLS), EB, 0, st>>>(w.A, k, j, w.tau, w.p);
-  }
-  hh_tail<<<1, 32, 0, st>>>(w.A, k, w.d, w.e, w.tau);
-  DOPINF_TRY(launch_status());
+  DOPINF_TRY(tridiagonalise(w, k, st));
   tri_multisect<<<(r_cap + 3) / 4, 128, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm);
   tri_invit<<<(r_cap + 63) / 64, 64, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.Dg, w.Du, w.Du2, w.Dl, w.piv,
                                              w.Z);
@@ -446,7 +657,13 @@ DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double ene
   double tr_host = 0.0;
   DOPINF_CUDA(cudaMemcpyAsync(&r_host, w.r, sizeof(int), cudaMemcpyDeviceToHost, st));
   DOPINF_CUDA(cudaMemcpyAsync(&tr_host, w.trace, sizeof(double), cudaMemcpyDeviceToHost, st));
+  unsigned bar_err = 0;
+  DOPINF_CUDA(cudaMemcpyAsync(&bar_err, &w.bar->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   DOPINF_CUDA(cudaStreamSynchronize(st));
+  if (bar_err) {
+    set_last_error("dopinf_reduce: grid barrier of the tridiagonalisation", cudaErrorTimeout);
+    return DOPINF_E_TIMEOUT;
+  }
   *trace_out = tr_host;
   if (r_host == 0) {
     *r_out = 0;

@@ -3,11 +3,11 @@
 // Ogita, Oishi and Rump, "Error-free transformations of matrix multiplication", 2012).
 //
 // GB300 has about 1.1 TFLOP/s of FP64 but ~2 PFLOP/s of BF16 tensor throughput.  Each column a
-// of Q is scaled by 2^-s_a (s_a the exponent bounding its max-abs), and each scaled value
-// v in (-1, 1) is cut into S = 8 digits of 7 bits:
-//     t = v * 2^7, d_1 = rint(t), v_1 = t - d_1,  t = v_1 * 2^7, d_2 = rint(t), ...
-// so x = 2^s_a * sum_i d_i 2^(-7 i) + e with |e| <= 2^(s_a - 57), every step exact in FP64.
-// |d_1| <= 128 and |d_i| <= 64 for i > 1 are integers, exact in BF16.  Then
+// of Q is scaled by 2^-s_a (s_a the exponent bounding its max-abs) and rounded to a 56-bit
+// fixed-point integer V, which is cut into S = 8 balanced base-128 digits (integer arithmetic
+// on the IEEE encoding; the FP64 pipe is not used):
+//     x = 2^s_a * sum_i d_i 2^(-7 i) + e,  |e| <= 2^(s_a - 57),
+// with |d_1| <= 128 and |d_i| <= 64 for i > 1, integers exact in BF16.  Then
 //     D_ab = 2^(s_a + s_b) * sum_w 2^(-7 w) S_w,   S_w = sum_{i + j = w} D_i^T D_j,
 // keeping the weights w = 2..9 (36 digit products; the dropped ones weigh <= 2^-70).
 // Each S_w is formed in a pass of its own: a product of two digits is at most 2^14, so a
@@ -80,44 +80,133 @@ __device__ __forceinline__ float two_sum_hi(float hi, float a, float& err) {
   return s;
 }
 
-// max |Q[:, a]| per column -> exponent s_a with max < 2^s_a (0 for an all-zero column)
+// Sign and magnitude bits of a value: x = sign * m * 2^(e - bias) with an integer significand m
+// (implicit bit included), read from the IEEE encoding with integer operations only.
+__device__ __forceinline__ void decode(double x, bool& neg, unsigned long long& m, int& e2) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  neg = (b >> 63) != 0;
+  const int ef = (int)((b >> 52) & 0x7ff);
+  m = b & 0xfffffffffffffull;
+  if (ef) m |= 1ull << 52;
+  e2 = (ef ? ef : 1) - 1075;  // x = m * 2^e2
+}
+__device__ __forceinline__ void decode(float x, bool& neg, unsigned long long& m, int& e2) {
+  const unsigned b = __float_as_uint(x);
+  neg = (b >> 31) != 0;
+  const int ef = (int)((b >> 23) & 0xff);
+  m = b & 0x7fffffu;
+  if (ef) m |= 1u << 23;
+  e2 = (ef ? ef : 1) - 150;
+}
+
+// max |Q[:, a]| per column, as the exponent s_a with max < 2^s_a (0 for an all-zero column).
+// Magnitudes compare as integers of their encodings.
 template <typename T>
 __global__ void __launch_bounds__(256) colmax_kernel(const T* __restrict__ Q, int64_t n, int64_t ldq, int* __restrict__ sexp) {
-  __shared__ double sh[256];
+  __shared__ unsigned long long sh[256];
   const int64_t a = blockIdx.x;
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)Q[i + a * ldq]));
-  sh[threadIdx.x] = m;
+  const T* q = Q + a * ldq;
+  auto mag = [](T x) -> unsigned long long {
+    if constexpr (sizeof(T) == 8)
+      return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    else
+      return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+  };
+  unsigned long long mb = 0, mb1 = 0, mb2 = 0, mb3 = 0;
+  const int64_t step = blockDim.x;
+  int64_t i = threadIdx.x;
+  for (; i + 3 * step < n; i += 4 * step) {  // four independent loads in flight per thread
+    const unsigned long long b0 = mag(q[i]), b1 = mag(q[i + step]), b2 = mag(q[i + 2 * step]), b3 = mag(q[i + 3 * step]);
+    mb = b0 > mb ? b0 : mb;
+    mb1 = b1 > mb1 ? b1 : mb1;
+    mb2 = b2 > mb2 ? b2 : mb2;
+    mb3 = b3 > mb3 ? b3 : mb3;
+  }
+  for (; i < n; i += step) {
+    const unsigned long long b = mag(q[i]);
+    mb = b > mb ? b : mb;
+  }
+  mb = mb1 > mb ? mb1 : mb;
+  mb = mb2 > mb ? mb2 : mb;
+  mb = mb3 > mb ? mb3 : mb;
+  sh[threadIdx.x] = mb;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) mx = fmax(mx, sh[i]);
+    unsigned long long mx = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) mx = sh[i] > mx ? sh[i] : mx;
     int e = 0;
-    if (mx > 0.0) {
-      frexp(mx, &e);  // mx = f 2^e with 0.5 <= f < 1, so mx < 2^e
+    if (mx) {
+      bool neg;
+      unsigned long long m;
+      int e2;
+      if constexpr (sizeof(T) == 8)
+        decode(__longlong_as_double((long long)mx), neg, m, e2);
+      else
+        decode(__uint_as_float((unsigned)mx), neg, m, e2);
+      e = e2 + 64 - __clzll((long long)m);  // m 2^e2 < 2^e
     }
     sexp[a] = e;
   }
 }
 
-// digits into the tiled planes: plane p at p * nrb * ncb * 8192, block (cb, rb) inside it
+// V = round(x 2^(56 - s)) as a signed integer (|V| <= 2^56 for |x| < 2^s, error <= 1/2).
 template <typename T>
-__global__ void digits_kernel(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq, const int* __restrict__ sexp,
-                              __nv_bfloat16* __restrict__ planes, int64_t nrb, int64_t ncb) {
+__device__ __forceinline__ long long fixed56(T x, int s) {
+  bool neg;
+  unsigned long long m;
+  int e2;
+  decode(x, neg, m, e2);
+  const int sh = e2 + 56 - s;  // V = m 2^sh
+  unsigned long long u;
+  if (sh >= 0)
+    u = m << sh;  // |x| < 2^s keeps this below 2^56
+  else if (sh > -64)
+    u = (m + (1ull << (-sh - 1))) >> (-sh);  // round half up in magnitude
+  else
+    u = 0;
+  return neg ? -(long long)u : (long long)u;
+}
+
+// Digits into the tiled planes (plane p at p * nrb * ncb * 8192, block (cb, rb) inside it), by
+// integer arithmetic: V = round(x 2^(56 - s_a)) (error <= 2^(s_a - 57) in x), then balanced
+// base-128 digits from the low end, d_8 .. d_2 in [-64, 63], and the rest d_1 with |d_1| <= 128,
+// so that V = sum_i d_i 2^(7 (8 - i)).  A thread takes 4 consecutive rows of one column and
+// writes 8 bytes per plane; blockIdx.y walks the (padded) columns.
+constexpr int DIG_ROWS = 4;
+template <typename T>
+__global__ void __launch_bounds__(256) digits_kernel(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq,
+                                                     const int* __restrict__ sexp, __nv_bfloat16* __restrict__ planes,
+                                                     int64_t nrb, int64_t ncb) {
   const int64_t rows = nrb * BK, cols = ncb * BM;
-  const int64_t total = rows * cols;
   const size_t plane = (size_t)nrb * ncb * BM * BK;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, t = e / rows;
-    double v = 0.0;
-    if (i < n && t < k) v = ldexp((double)Q[i + t * ldq], -sexp[t]);
-    const size_t off = (size_t)((t / BM) * nrb + i / BK) * (BM * BK) + (t % BM) * BK + (i % BK);
+  for (int64_t t = blockIdx.y; t < cols; t += gridDim.y) {
+    const T* q = Q + t * ldq;
+    const int s = t < k ? sexp[t] : 0;
+    const size_t cbase = (size_t)(t / BM) * nrb * (BM * BK) + (size_t)(t % BM) * BK;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * DIG_ROWS; i0 < rows;
+         i0 += (int64_t)gridDim.x * blockDim.x * DIG_ROWS) {
+      long long V[DIG_ROWS];
 #pragma unroll
-    for (int p = 0; p < NDIG; ++p) {
-      const double tt = v * (double)(1 << DIG_BITS);
-      const double d = rint(tt);
-      v = tt - d;
-      planes[p * plane + off] = __double2bfloat16(d);
+      for (int u = 0; u < DIG_ROWS; ++u) V[u] = (t < k && i0 + u < n) ? fixed56(q[i0 + u], s) : 0;
+      // i0 is a multiple of 4 and BK of 64: the 4 rows sit in one block, 8-byte aligned
+      __nv_bfloat16* dst = planes + cbase + (size_t)(i0 / BK) * (BM * BK) + (i0 % BK);
+#pragma unroll
+      for (int p = NDIG - 1; p >= 0; --p) {
+        __nv_bfloat16 h[DIG_ROWS];
+#pragma unroll
+        for (int u = 0; u < DIG_ROWS; ++u) {
+          long long d = V[u];
+          if (p > 0) {
+            d = ((V[u] + 64) & 127) - 64;
+            V[u] = (V[u] - d) >> DIG_BITS;
+          }
+          h[u] = __float2bfloat16_rn((float)d);
+        }
+        uint2 pk;
+        pk.x = (unsigned)__bfloat16_as_ushort(h[0]) | ((unsigned)__bfloat16_as_ushort(h[1]) << 16);
+        pk.y = (unsigned)__bfloat16_as_ushort(h[2]) | ((unsigned)__bfloat16_as_ushort(h[3]) << 16);
+        *reinterpret_cast<uint2*>(dst + p * plane) = pk;
+      }
     }
   }
 }
@@ -428,14 +517,21 @@ int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
   else
     colmax_kernel<float><<<(unsigned)k, 256, 0, st>>>(static_cast<const float*>(Q), n, ldq, w.sexp);
   DOPINF_TRY(launch_status());
-  const int64_t total = sh.nrb * BK * sh.ncb * BM;
-  const unsigned dblocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
-  if (dtype == DOPINF_F64)
-    digits_kernel<double><<<dblocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.sexp, w.planes, sh.nrb,
-                                                    sh.ncb);
-  else
-    digits_kernel<float><<<dblocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.sexp, w.planes, sh.nrb,
-                                                   sh.ncb);
+  {
+    // rows split in chunks of 256 threads x 4 rows, enough CTAs for ~32 per SM over all columns
+    const int64_t rows = sh.nrb * BK, cols = sh.ncb * BM;
+    const int64_t xb_need = (rows + 1023) / 1024;
+    const int64_t ycols = cols < 65535 ? cols : 65535;
+    int64_t xb = (152 * 32 + ycols - 1) / ycols;
+    xb = xb < 1 ? 1 : (xb > xb_need ? xb_need : xb);
+    const dim3 grid((unsigned)xb, (unsigned)ycols);
+    if (dtype == DOPINF_F64)
+      digits_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.sexp, w.planes, sh.nrb,
+                                                  sh.ncb);
+    else
+      digits_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.sexp, w.planes, sh.nrb,
+                                                 sh.ncb);
+  }
   DOPINF_TRY(launch_status());
   CUtensorMap map;
   if (!make_map(&map, w.planes, (int64_t)NDIG * sh.nrb * sh.ncb)) return DOPINF_E_CUDA;

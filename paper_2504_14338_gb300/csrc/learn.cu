@@ -8,18 +8,19 @@
 //                   (continuous);
 //   tn_product      G = Dhat^T Dhat (symmetric) and B = Dhat^T Y in FP64;
 //   train_stats     temporal mean mu of the reference and max_{t<k,i} |qhat - mu|;
-//   chol_solve      one CTA per (beta1, beta2): (G + diag(reg)) X = B by Cholesky, O = X^T;
-//   rollouts        one CTA per candidate with the fused training error / growth epilogue.
+// Then schur_solve (schur.cu) solves (G + diag(reg)) O^T = B for every (r, beta1, beta2) by
+// block elimination of the quadratic unknowns, shared across beta1, and the rollouts run every
+// candidate (a thread-block cluster each) with the fused training error / growth epilogue.
 // Then select_best takes the lowest training error among valid candidates (lowest index on
 // ties).  Everything is FP64.
 #include "common.cuh"
 #include <math.h>
+#include <vector>
 
 namespace dopinf {
 namespace {
 
 constexpr int LB = 256;
-constexpr int CB = 512;
 
 __global__ void __launch_bounds__(LB) build_features(const double* __restrict__ Qhat, int64_t ldqh, int r, int d,
                                                      int64_t K, int64_t t0, int mode, double dt,
@@ -80,88 +81,6 @@ __global__ void __launch_bounds__(LB) train_stats(const double* __restrict__ Qha
   }
 }
 
-// One CTA per candidate (every r and pair in one launch).  M (d x d) and X (d x r) live in
-// the workspace (L2-resident for the sizes of Step IV).  Right-looking Cholesky M = L L^T, then
-// L Z = B, L^T X = Z.  A non-positive or non-finite pivot marks the candidate (status 1).
-struct CholCand {
-  const double* G;  // d x d normal matrix of this candidate's r
-  const double* B;  // d x r right-hand sides
-  double* M;        // d x d scratch (factorised in place)
-  double* X;        // d x r solution
-  double* O;        // r x d operator output (ld r)
-  double b1, b2;
-  int r, d, cand;
-};
-
-__global__ void __launch_bounds__(CB) chol_solve(const CholCand* __restrict__ table, int* __restrict__ status) {
-  __shared__ int s_fail;
-  const CholCand cc = table[blockIdx.x];
-  const int r = cc.r, d = cc.d, s = d - r - 1;
-  double* M = cc.M;
-  double* X = cc.X;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = CB / 32;
-  for (int64_t e = tid; e < (int64_t)d * d; e += CB) {
-    const int i = (int)(e % d), c = (int)(e / d);
-    double v = cc.G[e];
-    if (i == c) v += (i < r || i == r + s) ? cc.b1 : cc.b2;
-    M[e] = v;
-  }
-  for (int64_t e = tid; e < (int64_t)d * r; e += CB) X[e] = cc.B[e];
-  if (tid == 0) s_fail = 0;
-  __syncthreads();
-  for (int j = 0; j < d; ++j) {
-    const double piv = M[j + (size_t)j * d];
-    if (!(piv > 0.0) || !isfinite(piv)) {
-      if (tid == 0) s_fail = 1;
-      break;
-    }
-    const double ljj = sqrt(piv), inv = 1.0 / ljj;
-    for (int i = j + 1 + tid; i < d; i += CB) M[i + (size_t)j * d] *= inv;
-    __syncthreads();
-    if (tid == 0) M[j + (size_t)j * d] = ljj;
-    for (int c = j + 1 + w; c < d; c += nw) {
-      const double lc = M[c + (size_t)j * d];
-      double* col = M + (size_t)c * d;
-      const double* lj = M + (size_t)j * d;
-      for (int i = c + lane; i < d; i += 32) col[i] = fma(-lj[i], lc, col[i]);
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  if (s_fail) {
-    if (tid == 0) status[cc.cand] = 1;
-    return;
-  }
-  // forward: L Z = B (column j of L scales row j, then updates the rows below)
-  for (int j = 0; j < d; ++j) {
-    const double inv = 1.0 / M[j + (size_t)j * d];
-    for (int c = tid; c < r; c += CB) X[j + (size_t)c * d] *= inv;
-    __syncthreads();
-    const int64_t rows = d - j - 1;
-    for (int64_t e = tid; e < rows * r; e += CB) {
-      const int i = j + 1 + (int)(e % rows), c = (int)(e / rows);
-      X[i + (size_t)c * d] = fma(-M[i + (size_t)j * d], X[j + (size_t)c * d], X[i + (size_t)c * d]);
-    }
-    __syncthreads();
-  }
-  // backward: L^T X = Z
-  for (int j = d - 1; j >= 0; --j) {
-    const double inv = 1.0 / M[j + (size_t)j * d];
-    for (int c = tid; c < r; c += CB) X[j + (size_t)c * d] *= inv;
-    __syncthreads();
-    for (int64_t e = tid; e < (int64_t)j * r; e += CB) {
-      const int i = (int)(e % j), c = (int)(e / j);
-      X[i + (size_t)c * d] = fma(-M[j + (size_t)i * d], X[j + (size_t)c * d], X[i + (size_t)c * d]);
-    }
-    __syncthreads();
-  }
-  for (int64_t e = tid; e < (int64_t)r * d; e += CB) {
-    const int i = (int)(e % r), a = (int)(e / r);
-    cc.O[e] = X[a + (size_t)i * d];
-  }
-  if (tid == 0) status[cc.cand] = 0;
-}
-
 __global__ void select_best(const double* err, const int* status, int n_cand, int* best) {
   if (threadIdx.x != 0) return;
   int b = -1;
@@ -176,16 +95,18 @@ constexpr int kMaxR = 64;  // entries of the r list
 
 // Workspace layout, one for the size query (base == nullptr) and for the entry point.
 struct LearnWs {
-  CholCand* chol;
+  SchurUnit* units;
+  SchurCand* cands;
   RolloutCand* roll;
   double *mu, *denom, *Dh, *Y;
-  double *G[kMaxR], *B[kMaxR], *M[kMaxR], *X[kMaxR], *O[kMaxR];
-  int* best;
+  double *G[kMaxR], *B[kMaxR], *E[kMaxR], *S[kMaxR], *O[kMaxR];
+  int *best, *unit_fail;
   void* tn;
   size_t tn_bytes, used;
 };
 
-LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_pairs) {
+LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1, int n_b2) {
+  const int n_pairs = n_b1 * n_b2;
   Carver c(base);
   LearnWs w;
   int d_max = 0, r_max = 0;
@@ -194,8 +115,10 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_pai
     if (r_list[i] > r_max) r_max = r_list[i];
   }
   const int n_cand = n_r * n_pairs;
-  w.chol = c.take<CholCand>(n_cand);
+  w.units = c.take<SchurUnit>((size_t)n_r * n_b2);
+  w.cands = c.take<SchurCand>(n_cand);
   w.roll = c.take<RolloutCand>(n_cand);
+  w.unit_fail = c.take<int>((size_t)n_r * n_b2);
   w.mu = c.take<double>((size_t)n_r * r_max);
   w.denom = c.take<double>(n_r);
   w.best = c.take<int>(1);
@@ -205,8 +128,8 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_pai
     const size_t r = r_list[i], d = dim_d(r_list[i]);
     w.G[i] = c.take<double>(d * d);
     w.B[i] = c.take<double>(d * r);
-    w.M[i] = c.take<double>((size_t)n_pairs * d * d);
-    w.X[i] = c.take<double>((size_t)n_pairs * d * r);
+    w.E[i] = c.take<double>((size_t)n_b2 * schur_unit_doubles((int)r));
+    w.S[i] = c.take<double>((size_t)n_pairs * schur_cand_doubles((int)r));
     w.O[i] = c.take<double>((size_t)n_pairs * r * d);
   }
   size_t tb = 0;
@@ -241,7 +164,7 @@ static int64_t learn_rows(int64_t k, int mode) { return mode == DOPINF_DISCRETE 
 DOPINF_API size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1, int n_b2) {
   (void)r_max;
   if (!r_list || n_r < 1 || n_r > kMaxR || n_b1 < 1 || n_b2 < 1 || k < 3) return 0;
-  return carve_learn(nullptr, k - 1, r_list, n_r, n_b1 * n_b2).used;
+  return carve_learn(nullptr, k - 1, r_list, n_r, n_b1, n_b2).used;
 }
 
 DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
@@ -271,24 +194,39 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
   if (!cluster) return DOPINF_E_UNSUPPORTED;
   cudaStream_t st = as_stream(stream);
   // the workspace is laid out for K = k - 1 rows, which covers both modes
-  LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1 * n_b2);
+  LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1, n_b2);
   const int n_pairs = n_b1 * n_b2, n_cand = n_r * n_pairs;
-  // candidate tables, built on the host: c = (ir * n_b1 + i1) * n_b2 + i2
-  CholCand* ch = new CholCand[n_cand];
+  // candidate tables, built on the host: c = (ir * n_b1 + i1) * n_b2 + i2; unit = ir * n_b2 + i2
+  const int n_units = n_r * n_b2;
+  std::vector<SchurUnit> un(n_units);
+  SchurCand* ch = new SchurCand[n_cand];
   RolloutCand* ro = new RolloutCand[n_cand];
   for (int ir = 0; ir < n_r; ++ir) {
-    const int r = r_list[ir], d = dim_d(r);
+    const int r = r_list[ir], d = dim_d(r), sq = r * (r + 1) / 2, N = sq + 2 * r + 1;
+    for (int i2 = 0; i2 < n_b2; ++i2) {
+      SchurUnit& U = un[ir * n_b2 + i2];
+      U.G = w.G[ir];
+      U.B = w.B[ir];
+      U.E = w.E[ir] + (size_t)i2 * schur_unit_doubles(r);
+      U.b2 = beta2[i2];
+      U.r = r;
+      U.d = d;
+      U.s = sq;
+      U.m = r + 1;
+      U.N = N;
+      U.unit = ir * n_b2 + i2;
+    }
     for (int p = 0; p < n_pairs; ++p) {
-      const int c = ir * n_pairs + p;
-      ch[c].G = w.G[ir];
-      ch[c].B = w.B[ir];
-      ch[c].M = w.M[ir] + (size_t)p * d * d;
-      ch[c].X = w.X[ir] + (size_t)p * d * r;
+      const int c = ir * n_pairs + p, i2 = p % n_b2;
+      ch[c].E = un[ir * n_b2 + i2].E;
       ch[c].O = w.O[ir] + (size_t)p * r * d;
+      ch[c].scratch = w.S[ir] + (size_t)p * schur_cand_doubles(r);
       ch[c].b1 = beta1[p / n_b2];
-      ch[c].b2 = beta2[p % n_b2];
       ch[c].r = r;
-      ch[c].d = d;
+      ch[c].s = sq;
+      ch[c].m = r + 1;
+      ch[c].N = N;
+      ch[c].unit = ir * n_b2 + i2;
       ch[c].cand = c;
       ro[c].O = ch[c].O;
       ro[c].ldo = r;
@@ -300,10 +238,12 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     }
   }
   // pageable host -> device copies: the runtime stages the source before returning
-  cudaError_t e1 = cudaMemcpyAsync(w.chol, ch, sizeof(CholCand) * n_cand, cudaMemcpyHostToDevice, st);
+  cudaError_t e0 = cudaMemcpyAsync(w.units, un.data(), sizeof(SchurUnit) * n_units, cudaMemcpyHostToDevice, st);
+  cudaError_t e1 = cudaMemcpyAsync(w.cands, ch, sizeof(SchurCand) * n_cand, cudaMemcpyHostToDevice, st);
   cudaError_t e2 = cudaMemcpyAsync(w.roll, ro, sizeof(RolloutCand) * n_cand, cudaMemcpyHostToDevice, st);
   delete[] ch;
   delete[] ro;
+  DOPINF_CUDA(e0);
   DOPINF_CUDA(e1);
   DOPINF_CUDA(e2);
   const int64_t t0 = mode == DOPINF_DISCRETE ? 0 : 1;
@@ -318,8 +258,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * r_max, w.denom + ir);
     DOPINF_TRY(launch_status());
   }
-  chol_solve<<<n_cand, CB, 0, st>>>(w.chol, cand_status);
-  DOPINF_TRY(launch_status());
+  DOPINF_TRY(schur_solve(w.units, un.data(), n_units, w.cands, n_cand, w.unit_fail, cand_status, st));
   RolloutBatch bt = {};
   bt.cands = w.roll;
   bt.n_cand = n_cand;

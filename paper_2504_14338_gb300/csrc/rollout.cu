@@ -11,7 +11,8 @@
 // everywhere.  The stage results are double-buffered by step parity, so a CTA that runs ahead
 // never overwrites values a slower peer is still reading.  The RK4 combination, the metrics
 // and the early-exit decision are computed identically in every CTA, so the cluster stays in
-// lockstep without further communication.
+// lockstep without further communication.  FP64 throughput per SM is small on GB300, so each
+// stage state is formed once (r values) before its feature build rather than inside it.
 #include "common.cuh"
 #include <cooperative_groups.h>
 #include <math.h>
@@ -25,7 +26,7 @@ constexpr int RB = 256;  // threads per CTA
 constexpr int NW = RB / 32;
 
 struct SmemLayout {
-  size_t o, q, xs, kb, phi, pi, pj, total;
+  size_t o, q, xs, kb, phi, mu, pi, pj, total;
 };
 
 // Shared layout for a CTA holding rc operator rows of width d_max, vectors of r_max.
@@ -42,6 +43,8 @@ __host__ __device__ inline SmemLayout smem_layout(int rc, int r_max, int d_max) 
   off += (size_t)8 * r_max * sizeof(double);
   L.phi = off;
   off += (size_t)d_max * sizeof(double);
+  L.mu = off;
+  off += (size_t)r_max * sizeof(double);
   const int s_max = d_max - r_max - 1 > 0 ? d_max - r_max - 1 : 1;
   L.pi = off;
   off += (size_t)s_max * sizeof(unsigned short);
@@ -101,6 +104,7 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
   double* xs = reinterpret_cast<double*>(smraw + L.xs);
   double* kb = reinterpret_cast<double*>(smraw + L.kb);
   double* phi = reinterpret_cast<double*>(smraw + L.phi);
+  double* mu = reinterpret_cast<double*>(smraw + L.mu);
   unsigned short* pi = reinterpret_cast<unsigned short*>(smraw + L.pi);
   unsigned short* pj = reinterpret_cast<unsigned short*>(smraw + L.pj);
   __shared__ int s_stop;
@@ -124,7 +128,10 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
       pj[off + j - i] = (unsigned short)j;
     }
   }
-  for (int i = threadIdx.x; i < r; i += RB) q[i] = bt.q0[i];
+  for (int i = threadIdx.x; i < r; i += RB) {
+    q[i] = bt.q0[i];
+    mu[i] = bt.metrics ? cd.mu[i] : 0.0;
+  }
   if (threadIdx.x == 0) s_stop = 0;
   cl.sync();  // every CTA initialised before any remote store
 
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
         const double v = q[i];
         fin = fin && isfinite(v);
         if (bt.metrics) {
-          dev = fmax(dev, fabs(v - cd.mu[i]));
+          dev = fmax(dev, fabs(v - mu[i]));
           if (t < bt.k) {
             const double h = bt.Qhat[i + t * bt.ldqh];
             num += (v - h) * (v - h);

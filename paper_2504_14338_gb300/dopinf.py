@@ -66,6 +66,7 @@ def _load():
                                         ctypes.POINTER(ctypes.c_int), _c_p, _c_p, _c_sz, _c_p]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_tune_learn_cluster": (ctypes.c_int, [ctypes.c_int]),
+        "dopinf_tune_reduce_coop": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_rollout": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_p, _c_i64, ctypes.c_int,
                                           ctypes.c_double, _c_p, _c_p, _c_p]),
         "dopinf_proposal_features": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.c_double, _c_p, ctypes.c_int,
@@ -189,6 +190,12 @@ def dopinf_tune_gram_chunk(rows=0):
 def dopinf_tune_learn_cluster(cluster=0):
     """Sets (1, 2, 4, 8) or queries the rollout cluster size of dopinf_learn; returns the previous value."""
     return int(lib.dopinf_tune_learn_cluster(int(cluster)))
+
+
+def dopinf_tune_reduce_coop(on=-1):
+    """Sets (1: one cooperative launch, 0: three launches per column) or queries the
+    tridiagonalisation of dopinf_reduce; returns the previous value."""
+    return int(lib.dopinf_tune_reduce_coop(int(on)))
 
 
 def dopinf_reduce(D, r_cap, energy_target=0.9996, r_fixed=0, ws=None, stream=None):

@@ -1,5 +1,6 @@
 """Parity at the benchmark's full size (2D step-flow shape: n = 1.2M rows, k = 600,
-r in {10, 20, 30}, 8 x 8 grid, 5000-step RK4), in the launch configuration bench.py times,
+r in {10, 20, 30}, 8 x 8 grid, 5000-step RK4), in the launch configuration bench.py times
+(FP64-accurate digit-product Gram on the tensor cores, cluster rollouts),
 on outputs the FP64 oracle can compute one by one: sampled rows of the transform, sampled
 Gram entries, the whole k x k eigenproblem, and a sample of the learn candidates."""
 import numpy as np
@@ -30,7 +31,7 @@ def run():
     raw = Q[torch.from_numpy(rows).cuda()].cpu().numpy()
     ws = dp.Workspace("cuda")
     mean, scale, flags = dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
-    D = dp.dopinf_gram(Q, ws=ws)
+    D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws)   # the Gram mode bench.py times
     red = dp.dopinf_reduce(D, r_cap=max(w.r_list), r_fixed=max(w.r_list), ws=ws)
     b1, b2 = w.beta1s(), w.beta2s()
     res = dp.dopinf_learn(red["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=dp.CONTINUOUS_RK4,

@@ -229,6 +229,25 @@ def test_reduce_vs_oracle(dp, k, r_cap):
             assert err <= 1e3 * k * EPS * lam_ref[0] / gap + 1e-10, (j, err)
 
 
+@pytest.mark.parametrize("k", [3, 4, 9, 200, 601])
+def test_reduce_cooperative_matches_per_column_launches(dp, k):
+    """The one-launch tridiagonalisation (grid barrier per column) gives the same bits as
+    three launches per column."""
+    rng = np.random.default_rng(100 + k)
+    X = rng.standard_normal((2 * k, k)) @ np.diag(1.1 ** -np.arange(k))
+    Dd = torch.from_numpy(X.T @ X).cuda()
+    r_cap = min(k, 8)
+    prev = dp.dopinf_tune_reduce_coop(1)
+    try:
+        a = dp.dopinf_reduce(Dd, r_cap=r_cap, r_fixed=r_cap)
+        dp.dopinf_tune_reduce_coop(0)
+        b = dp.dopinf_reduce(Dd, r_cap=r_cap, r_fixed=r_cap)
+    finally:
+        dp.dopinf_tune_reduce_coop(prev)
+    for key in ("eigvals", "Tr", "Qhat"):
+        assert torch.equal(a[key], b[key]), key
+
+
 def test_reduce_energy_rank_and_pipeline_qhat(dp):
     D, _ = _pipeline_D()
     ref = O.reduce(D, tau=0.9996, r_cap=None)
