@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--pipeline-gram", default="ozaki", choices=["fp64", "ozaki"],
                    help="FP64-accurate Gram of the pipeline: FP64 pipe, or exact digit products on the tensor cores")
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential grid-search baseline")
+    p.add_argument("--n-steps", type=int, default=0, help="override the rollout length of --stage learn")
+    p.add_argument("--r-list", default="", help="override the r list of --stage learn, e.g. 30 or 10,20")
+    p.add_argument("--cluster", type=int, default=0, help="--stage learn: rollout cluster size (1, 2, 4, 8; 0: default)")
     return p.parse_args()
 
 
@@ -335,13 +338,17 @@ def main():
                               "useful_tflops": w.n * w.k * (w.k + 1) / ms / 1e9}), flush=True)
         return
     if args.stage == "learn":
+        r_list = [int(x) for x in args.r_list.split(",")] if args.r_list else list(w.r_list)
+        n_steps = args.n_steps or w.n_steps
+        if args.cluster:
+            dp.dopinf_tune_learn_cluster(args.cluster)
         dp.dopinf_transform(Q, offs, ws=ws)
         red = dp.dopinf_reduce(dp.dopinf_gram(Q, ws=ws), r_cap=r_max, r_fixed=r_max, ws=ws)
         times = []
         for i in range(args.warmup + args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            res = dp.dopinf_learn(red["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode, dt=w.snap_dt, ws=ws)
+            res = dp.dopinf_learn(red["Qhat"], r_list, b1, b2, n_steps, mode=mode, dt=w.snap_dt, ws=ws)
             b.record(stream)
             torch.cuda.synchronize()
             if i >= args.warmup:
@@ -349,7 +356,8 @@ def main():
         st = res["status"].cpu().numpy()
         if rank == 0:
             print(json.dumps({"stage": "learn", "ms": float(np.mean(times)), "best": res["best"],
-                              "valid": int((st == 0).sum()), "n_cand": int(st.size)}), flush=True)
+                              "valid": int((st == 0).sum()), "n_cand": int(st.size), "r_list": r_list,
+                              "n_steps": n_steps, "cluster": args.cluster}), flush=True)
         return
 
     last = {}

@@ -589,8 +589,9 @@ int tridiagonalise(const ReduceWs& w, int64_t k, cudaStream_t st) {
     int per_sm = 0;
     DOPINF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_tridiag_coop, TB, smem));
     if (per_sm >= 1) {
-      // about one warp per trailing column, at most one CTA per SM (a cheap barrier)
-      int64_t grid = (k - 1 + (TB / 32) - 1) / (TB / 32);
+      // FP64 throughput per SM binds: about four trailing columns per CTA (one warp on each
+      // of the SM's four schedulers), at most one CTA per SM (a cheap barrier)
+      int64_t grid = (k - 1 + 3) / 4;
       if (grid > sms) grid = sms;
       if (grid < 1) grid = 1;
       double* A = w.A;
@@ -642,9 +643,10 @@ DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double ene
   DOPINF_CUDA(cudaMemcpy2DAsync(w.A, k * sizeof(double), D, ldd * sizeof(double), k * sizeof(double), k,
                                 cudaMemcpyDeviceToDevice, st));
   DOPINF_TRY(tridiagonalise(w, k, st));
-  tri_multisect<<<(r_cap + 3) / 4, 128, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm);
-  tri_invit<<<(r_cap + 63) / 64, 64, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.Dg, w.Du, w.Du2, w.Dl, w.piv,
-                                             w.Z);
+  // one eigenvalue (a warp) and one eigenvector (a thread) per CTA: both are chains of FP64
+  // divisions, so they are spread over the SMs rather than packed into a few warps
+  tri_multisect<<<r_cap, 32, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm);
+  tri_invit<<<r_cap, 1, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.Dg, w.Du, w.Du2, w.Dl, w.piv, w.Z);
   tri_orth<<<1, EB, 0, st>>>(k, r_cap, w.lam, w.tnorm, w.Z);
   const size_t smem = (size_t)k * sizeof(double);
   if (smem > 48 * 1024) DOPINF_CUDA(cudaFuncSetAttribute(hh_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

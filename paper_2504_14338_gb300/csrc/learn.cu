@@ -100,6 +100,7 @@ struct LearnWs {
   RolloutCand* roll;
   double *mu, *denom, *Dh, *Y;
   double *G[kMaxR], *B[kMaxR], *E[kMaxR], *S[kMaxR], *O[kMaxR];
+  int r_stride;  // largest r of the list: stride of the per-r vectors (mu)
   int *best, *unit_fail;
   void* tn;
   size_t tn_bytes, used;
@@ -115,6 +116,7 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1,
     if (r_list[i] > r_max) r_max = r_list[i];
   }
   const int n_cand = n_r * n_pairs;
+  w.r_stride = r_max;
   w.units = c.take<SchurUnit>((size_t)n_r * n_b2);
   w.cands = c.take<SchurCand>(n_cand);
   w.roll = c.take<RolloutCand>(n_cand);
@@ -233,7 +235,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
       ro[c].r = r;
       ro[c].d = d;
       ro[c].cand = c;
-      ro[c].mu = w.mu + (size_t)ir * r_max;
+      ro[c].mu = w.mu + (size_t)ir * w.r_stride;
       ro[c].denom = w.denom + ir;
     }
   }
@@ -255,7 +257,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     DOPINF_TRY(launch_status());
     DOPINF_TRY(tn_product(w.Dh, K, w.Dh, K, DOPINF_F64, K, d, d, 1, 0, w.G[ir], d, w.tn, w.tn_bytes, st));
     DOPINF_TRY(tn_product(w.Dh, K, w.Y, K, DOPINF_F64, K, d, r, 0, 0, w.B[ir], d, w.tn, w.tn_bytes, st));
-    train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * r_max, w.denom + ir);
+    train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * w.r_stride, w.denom + ir);
     DOPINF_TRY(launch_status());
   }
   DOPINF_TRY(schur_solve(w.units, un.data(), n_units, w.cands, n_cand, w.unit_fail, cand_status, st));

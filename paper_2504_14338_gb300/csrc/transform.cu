@@ -156,6 +156,20 @@ __global__ void finalize_scale(double* var_scale, int n_vars, int scale, unsigne
   var_scale[v] = s;
 }
 
+// c / s rounded to nearest from y = RN(1/s), by Markstein's correction (P. Markstein, "Computation
+// of elementary functions on the IBM RISC System/6000 processor", IBM J. Res. Dev. 34(1), 1990):
+// q0 = RN(c y) lies within one ulp of c / s, the remainder c - s q0 is exact as one FMA, and
+// RN(q0 + rem y) is the correctly rounded quotient.  Three FP64 operations instead of a full
+// division; operands near the ends of the exponent range (zero, subnormal, huge, non-finite)
+// take the IEEE division, so the result equals c / s bit for bit everywhere.
+__device__ __forceinline__ double div_by(double c, double s, double y, bool s_ok) {
+  const double a = fabs(c);
+  if (!s_ok || !(a >= 0x1p-900 && a <= 0x1p+900)) return __ddiv_rn(c, s);
+  const double q0 = __dmul_rn(c, y);
+  const double rem = __fma_rn(-q0, s, c);
+  return __fma_rn(rem, y, q0);
+}
+
 // One thread per row and a chunk of columns; grid.y walks the columns.
 template <typename T>
 __global__ void __launch_bounds__(256) apply_kernel(T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq,
@@ -166,14 +180,16 @@ __global__ void __launch_bounds__(256) apply_kernel(T* __restrict__ Q, int64_t n
   if (i >= n) return;
   double m = center ? mean[i] : 0.0;
   double s = var_scale[var_of(vt, i)];
+  const double y = __ddiv_rn(1.0, s);
+  const bool s_ok = fabs(s) >= 0x1p-500 && fabs(s) <= 0x1p+500;
   int64_t t0 = (int64_t)blockIdx.y * cols_per_block;
   int64_t t1 = t0 + cols_per_block < k ? t0 + cols_per_block : k;
   T* p = Q + i;
   for (int64_t t = t0; t < t1; ++t) {
     T x = p[t * ldq];
     if constexpr (sizeof(T) == 8) {
-      double c = center ? (double)x - m : (double)x;
-      if (scale) c = c / s;
+      double c = center ? __dsub_rn((double)x, m) : (double)x;
+      if (scale) c = div_by(c, s, y, s_ok);
       p[t * ldq] = (T)c;
     } else {
       float c = center ? (float)((double)x - m) : (float)x;

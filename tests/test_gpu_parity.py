@@ -306,6 +306,24 @@ def test_learn_vs_oracle(dp, mode):
     assert ref["train_err"][best] <= ref["train_err"][ref["best"]] * (1 + 1e-6) + 1e-12
 
 
+def _learn_outputs(res):
+    return [res["train_err"], res["growth"], res["status"], res["O_best"]]
+
+
+def test_learn_ignores_extra_qhat_rows(dp):
+    """Qhat may hold more rows than the largest r of the list (every r uses its leading rows)."""
+    Qh = _reduced(r_fixed=12)
+    b1 = synth.logspace(-8, 2, 3)
+    b2 = synth.logspace(-8, 2, 3)
+    full = torch.from_numpy(Qh.T.copy()).cuda().t()
+    lead = torch.from_numpy(Qh[:6].T.copy()).cuda().t()
+    a = dp.dopinf_learn(full, [4, 6], b1, b2, 300)
+    b = dp.dopinf_learn(lead, [4, 6], b1, b2, 300)
+    assert a["best"] == b["best"]
+    for x, y in zip(_learn_outputs(a)[:3], _learn_outputs(b)[:3]):
+        assert torch.equal(x, y)
+
+
 def test_rollout_vs_oracle(dp):
     Qh = _reduced(r_fixed=5)
     Dh, Y = O.learning_data(Qh, 5)
