@@ -379,6 +379,7 @@ def main():
         e[4].record(stream)
         if record:
             ev.setdefault("stages", []).append(e)
+            ev.setdefault("learn_parts", []).append(res["stage_ms"])
         return res
 
     for _ in range(args.warmup):
@@ -441,25 +442,47 @@ def main():
         pass
     bf16 = peaks.get("bf16_tflops") or 1900.0
     fp64_peak = bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+    # dominant kernel of the step: the batched rollouts (FP64 pipe).  Algorithmic work per launch:
+    # 2 r d flop per right-hand-side evaluation x the evaluations each candidate ran (its steps
+    # x 4 for RK4), timed by the CUDA events dopinf_learn records around the launch.
+    steps_run = res["steps"].cpu().numpy()
+    n_pairs = len(b1) * len(b2)
+    evals = 4 if mode == dp.CONTINUOUS_RK4 else 1
+    roll_flops = 0
+    for c, st_c in enumerate(steps_run):
+        r_c = w.r_list[c // n_pairs]
+        roll_flops += int(st_c) * evals * 2 * r_c * (r_c + r_c * (r_c + 1) // 2 + 1)
+    roll_ms = float(np.mean([lp["rollouts"] for lp in ev["learn_parts"]]))
+    roll_gf = roll_flops / (roll_ms / 1e3) / 1e9
+    roof = {"kernel": "rollout_kernel (batched ROM rollouts, one cluster of 4 CTAs per candidate)", "bound": "alu",
+            "achieved": roll_gf, "peak": fp64_peak * 1e3, "unit": "GFLOP/s", "frac": roll_gf / (fp64_peak * 1e3),
+            "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)",
+            # dram__bytes_read + write of one ncu capture of this kernel on the same r, k, grid and
+            # horizon (the rollout's work does not depend on n): the operators, read once
+            "traffic": 10995200, "traffic_source": "profiles/rollout_kernel_stepflow_learn.md",
+            "algorithmic_flops_per_launch": roll_flops, "launch_ms": roll_ms,
+            "rhs_evaluations": int(steps_run.sum()) * evals}
+    # the Gram for context: the FP64-accurate Ozaki-digit product on the BF16 tensor cores
+    tn = (w.k + 127) // 128
+    executed = 36 * 2 * 128 * 128 * ((w.n + 63) // 64 * 64) * (tn * (tn + 1) // 2)
     if args.pipeline_gram == "ozaki":
-        # the digit products the kernel must execute for an FP64-exact D: 36 BF16 products over the
-        # 128 x 128 upper tiles of every 64-row block
-        tn = (w.k + 127) // 128
-        executed = 36 * 2 * 128 * 128 * ((w.n + 63) // 64 * 64) * (tn * (tn + 1) // 2)
         ach = executed / (stage["gram"] / 1e3) / 1e12
-        roof = {"kernel": "ozaki_pass_kernel x 8 + colmax/digits/reduce (FP64-accurate Gram)", "bound": "tensor",
-                "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                "peak_source": "measured bf16 burst (of measured)", "traffic": None,
-                "algorithmic_flops_per_launch": executed,
-                "fp64_equivalent_tflops": gram_tf, "fp64_equivalent_vs_fp64_peak": gram_tf / fp64_peak}
+        roof_gram = {"kernel": "ozaki_pass_kernel x 8 + colmax/digits/reduce (FP64-accurate Gram)", "bound": "tensor",
+                     "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                     "peak_source": "measured bf16 burst (of measured)", "algorithmic_flops_per_launch": executed,
+                     "fp64_equivalent_tflops": gram_tf, "fp64_equivalent_vs_fp64_peak": gram_tf / fp64_peak}
     else:
-        roof = {"kernel": "tn_partial (FP64 Gram, split-K) + tn_reduce", "bound": "alu", "achieved": gram_tf * 1e3,
-                "peak": fp64_peak * 1e3, "unit": "GFLOP/s", "frac": gram_tf / fp64_peak,
-                "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)",
-                "traffic": None, "algorithmic_flops_per_launch": gram_flops}
-    k = w.k
+        roof_gram = {"kernel": "tn_partial (FP64 Gram, split-K) + tn_reduce", "bound": "alu",
+                     "achieved": gram_tf * 1e3, "peak": fp64_peak * 1e3, "unit": "GFLOP/s",
+                     "frac": gram_tf / fp64_peak, "algorithmic_flops_per_launch": gram_flops}
+    # kernels the library launches per step (transform, Gram, reduce with the cooperative
+    # tridiagonalisation, learn: per r features + two TN products (2 each) + stats, the block-Schur
+    # solve (build, 3 per forward panel, back substitution, candidates), rollouts, selection)
     gram_launches = 11 if args.pipeline_gram == "ozaki" else 2
-    launches = 3 + gram_launches + (3 * (k - 2) + 8) + (6 * len(w.r_list) + 3)
+    s_max = max(w.r_list) * (max(w.r_list) + 1) // 2
+    panels = (s_max + 31) // 32
+    schur = 1 + 3 * panels + (2 * panels - 1) + 1
+    launches = 3 + gram_launches + 8 + (6 * len(w.r_list) + schur + 2)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         per, desc, wall = oracle_sample(w)
@@ -482,7 +505,7 @@ def main():
                 "stages_ms": stage, "pipeline_gram": args.pipeline_gram, "gram_useful_tflops": gram_tf,
                 "gram_modes": modes, "learn_s": stage["learn"] / 1e3,
                 "best": {"index": best, "r": res.get("r"), "beta1": res.get("beta1"), "beta2": res.get("beta2")},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "split_gram": split, "learn_vs_sequential": seq}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -194,7 +194,8 @@ int dopinf_tune_reduce_coop(int on);
  *   c = (ir * n_b1 + i1) * n_b2 + i2.
  * For each candidate: data matrix Dhat = [q, (q_i q_j)_{i<=j}, 1] over the training rows,
  * G = Dhat^T Dhat, B = Dhat^T Y, Cholesky solve of (G + diag(beta1 1_r, beta2 1_s,
- * beta1)) O^T = B; rollout of n_steps states (initial state included) from Qhat[:, 0];
+ * beta1)) O^T = B (by block elimination of the quadratic unknowns, which do not depend on
+ * beta1: the Cholesky factorisation of the symmetrically permuted matrix); rollout of n_steps states (initial state included) from Qhat[:, 0];
  * train_err = max_{t<k} ||q~_t - qhat_t|| / ||qhat_t||; growth = max_{t,i} |q~ - mu| /
  * max_{t<k,i} |qhat - mu| (mu = temporal mean of Qhat).  Valid iff the factorisation
  * succeeded, the rollout is finite and growth < max_growth.  A rollout stops early once
@@ -204,9 +205,15 @@ int dopinf_tune_reduce_coop(int on);
  * train_err, growth  out (device), n_cand doubles (+Inf for invalid candidates).
  * cand_status out (device), n_cand ints: 0 valid, 1 Cholesky breakdown, 2 non-finite,
  *            3 growth >= max_growth.
+ * cand_steps optional out (device, NULL = not wanted), n_cand int64: the time steps each
+ *            rollout advanced before it ended (n_steps - 1 for a valid candidate); the
+ *            right-hand-side evaluations are that times 4 (RK4) or 1 (discrete).
  * best_out   host: best candidate index, -1 if none is valid.
  * O_best     out (device), r_max x (d_max) doubles, ld r_max: operators [A | H | c] of
  *            the best candidate (its r x d leading block), d = r + r(r+1)/2 + 1.
+ * stage_ms   optional out (host, NULL = not wanted), 3 doubles: device time (CUDA events on
+ *            the stream) of the data matrices and normal equations, of the regularised
+ *            solves, and of the rollouts.
  * Synchronises the stream.  Returns DOPINF_E_NO_STABLE if no candidate is valid.
  * Workspace: dopinf_learn_workspace(...) bytes.
  * ------------------------------------------------------------------------------------ */
@@ -219,8 +226,8 @@ size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, 
 int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list,
                  int n_r, const double* beta1, int n_b1, const double* beta2, int n_b2,
                  int mode, double dt, int64_t n_steps, double max_growth, double* train_err,
-                 double* growth, int* cand_status, int* best_out, double* O_best, void* ws,
-                 size_t ws_bytes, void* stream);
+                 double* growth, int* cand_status, int64_t* cand_steps, int* best_out,
+                 double* O_best, double* stage_ms, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------
  * Rollout of one quadratic ROM (eq. ROM_quad_time_discrete, or RK4 on

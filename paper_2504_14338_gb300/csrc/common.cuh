@@ -128,6 +128,7 @@ struct RolloutBatch {
   double* train_err;
   double* growth;
   int* status;
+  int64_t* steps;  // optional: steps each rollout advanced (its RHS evaluations = steps x stages)
   // trajectory output (traj = 1): n_steps x r row-major; rows after the first non-finite
   // state are not written
   int traj;

@@ -172,7 +172,8 @@ DOPINF_API size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list
 DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
                             const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt,
                             int64_t n_steps, double max_growth, double* train_err, double* growth, int* cand_status,
-                            int* best_out, double* O_best, void* ws, size_t ws_bytes, void* stream) {
+                            int64_t* cand_steps, int* best_out, double* O_best, double* stage_ms, void* ws,
+                            size_t ws_bytes, void* stream) {
   if (!Qhat || r_max < 1 || ldqh < r_max || !r_list || n_r < 1 || n_r > kMaxR || !beta1 || !beta2 || n_b1 < 1 ||
       n_b2 < 1 || !train_err || !growth || !cand_status || !best_out || !O_best)
     return DOPINF_E_ARG;
@@ -248,6 +249,18 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
   DOPINF_CUDA(e0);
   DOPINF_CUDA(e1);
   DOPINF_CUDA(e2);
+  // optional stage timings (CUDA events on this stream): data + normal equations, solves, rollouts
+  cudaEvent_t ev[4] = {};
+  if (stage_ms)
+    for (int i = 0; i < 4; ++i) DOPINF_CUDA(cudaEventCreate(&ev[i]));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } ev_guard{ev};
+  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[0], st));
   const int64_t t0 = mode == DOPINF_DISCRETE ? 0 : 1;
   for (int ir = 0; ir < n_r; ++ir) {
     const int r = r_list[ir], d = dim_d(r);
@@ -260,7 +273,9 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * w.r_stride, w.denom + ir);
     DOPINF_TRY(launch_status());
   }
+  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[1], st));
   DOPINF_TRY(schur_solve(w.units, un.data(), n_units, w.cands, n_cand, w.unit_fail, cand_status, st));
+  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[2], st));
   RolloutBatch bt = {};
   bt.cands = w.roll;
   bt.n_cand = n_cand;
@@ -278,13 +293,21 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
   bt.train_err = train_err;
   bt.growth = growth;
   bt.status = cand_status;
+  bt.steps = cand_steps;
   DOPINF_TRY(launch_rollouts(bt, cluster, st));
+  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[3], st));
   select_best<<<1, 32, 0, st>>>(train_err, cand_status, n_cand, w.best);
   DOPINF_TRY(launch_status());
   int best = -1;
   DOPINF_CUDA(cudaMemcpyAsync(&best, w.best, sizeof(int), cudaMemcpyDeviceToHost, st));
   DOPINF_CUDA(cudaStreamSynchronize(st));
   *best_out = best;
+  if (stage_ms)
+    for (int i = 0; i < 3; ++i) {
+      float ms = 0.f;
+      DOPINF_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      stage_ms[i] = ms;
+    }
   if (best < 0) return DOPINF_E_NO_STABLE;
   const int ir = best / n_pairs, p = best % n_pairs, r = r_list[ir], d = dim_d(r);
   const double* src = w.O[ir] + (size_t)p * r * d;

@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
   const double denom = bt.metrics ? *cd.denom : 1.0;
   double err = 0.0, gnum = 0.0;
   int st = 0;
+  int64_t t_end = 0;  // the last state whose metrics were formed (= steps advanced)
   for (int64_t t = 0;; ++t) {
+    t_end = t;
     // ---- metrics and output of state t (warp 0 of every CTA, identical results) ----
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
   }
   cl.sync();  // no CTA leaves while a peer may still store into its shared memory
   if (rank == 0 && threadIdx.x == 0) {
+    if (bt.steps) bt.steps[cd.cand] = t_end;
     if (bt.metrics) {
       bt.status[cd.cand] = st;
       bt.train_err[cd.cand] = st == 0 ? err : INFINITY;

@@ -62,8 +62,9 @@ def _load():
         "dopinf_learn": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_double, _c_i64, ctypes.c_double, _c_p, _c_p, _c_p,
-                                        ctypes.POINTER(ctypes.c_int), _c_p, _c_p, _c_sz, _c_p]),
+                                        ctypes.c_double, _c_i64, ctypes.c_double, _c_p, _c_p, _c_p, _c_p,
+                                        ctypes.POINTER(ctypes.c_int), _c_p, ctypes.POINTER(ctypes.c_double), _c_p,
+                                        _c_sz, _c_p]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_tune_learn_cluster": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_reduce_coop": (ctypes.c_int, [ctypes.c_int]),
@@ -234,6 +235,8 @@ def dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=DISCRETE, dt=1.0, max
     err = torch.empty(n_cand, dtype=torch.float64, device=dev)
     gro = torch.empty(n_cand, dtype=torch.float64, device=dev)
     cst = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    steps = torch.zeros(n_cand, dtype=torch.int64, device=dev)
+    stage = (ctypes.c_double * 3)()
     d_max = max(r + r * (r + 1) // 2 + 1 for r in r_list)
     O_best = torch.zeros(d_max, r_max, dtype=torch.float64, device=dev).t()  # r_max x d_max column-major
     best = ctypes.c_int(-1)
@@ -241,9 +244,10 @@ def dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=DISCRETE, dt=1.0, max
     buf, nb = _ws(nb, ws, dev)
     st = lib.dopinf_learn(_ptr(Qhat), r_max, k, ldqh, rl, len(r_list), b1, len(beta1), b2, len(beta2), int(mode),
                           float(dt), int(n_steps), float(max_growth), _ptr(err), _ptr(gro), _ptr(cst),
-                          ctypes.byref(best), _ptr(O_best), _ptr(buf), nb, _stream(stream))
+                          _ptr(steps), ctypes.byref(best), _ptr(O_best), stage, _ptr(buf), nb, _stream(stream))
     _check("dopinf_learn", st, (OK, E_NO_STABLE) if allow_no_stable else (OK,))
-    out = dict(train_err=err, growth=gro, status=cst, best=best.value, O_best=O_best, code=st)
+    out = dict(train_err=err, growth=gro, status=cst, steps=steps, best=best.value, O_best=O_best, code=st,
+               stage_ms=dict(normal_equations=stage[0], solves=stage[1], rollouts=stage[2]))
     if best.value >= 0:
         nb12 = len(beta1) * len(beta2)
         r = int(r_list[best.value // nb12])

@@ -73,11 +73,11 @@ def test_arguments_rejected_before_launch():
     rl = (ctypes.c_int * 1)(3)
     b = (ctypes.c_double * 1)(1e-3)
     best = ctypes.c_int(0)
-    assert L.dopinf_learn(p8, 3, 50, 3, rl, 1, b, 1, b, 1, 0, 1.0, 10, 1.2, p8, p8, p8, ctypes.byref(best), p8,
-                          p8, 1 << 30, z) == dp.E_ARG
+    assert L.dopinf_learn(p8, 3, 50, 3, rl, 1, b, 1, b, 1, 0, 1.0, 10, 1.2, p8, p8, p8, z, ctypes.byref(best), p8,
+                          None, p8, 1 << 30, z) == dp.E_ARG
     rl4 = (ctypes.c_int * 1)(4)
-    assert L.dopinf_learn(p8, 3, 50, 3, rl4, 1, b, 1, b, 1, 0, 1.0, 100, 1.2, p8, p8, p8, ctypes.byref(best), p8,
-                          p8, 1 << 30, z) == dp.E_ARG
+    assert L.dopinf_learn(p8, 3, 50, 3, rl4, 1, b, 1, b, 1, 0, 1.0, 100, 1.2, p8, p8, p8, z, ctypes.byref(best), p8,
+                          None, p8, 1 << 30, z) == dp.E_ARG
     # rollout: r = 0, ldo < r
     assert L.dopinf_rollout(p8, 0, 1, p8, 10, 0, 1.0, p8, p8, z) == dp.E_ARG
     assert L.dopinf_rollout(p8, 3, 2, p8, 10, 0, 1.0, p8, p8, z) == dp.E_ARG
