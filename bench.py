@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--pipeline-gram", default="ozaki", choices=["fp64", "ozaki"],
                    help="FP64-accurate Gram of the pipeline: FP64 pipe, or exact digit products on the tensor cores")
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential grid-search baseline")
+    p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     p.add_argument("--n-steps", type=int, default=0, help="override the rollout length of --stage learn")
     p.add_argument("--r-list", default="", help="override the r list of --stage learn, e.g. 30 or 10,20")
     p.add_argument("--cluster", type=int, default=0, help="--stage learn: rollout cluster size (1, 2, 4, 8; 0: default)")
@@ -410,6 +411,26 @@ def main():
     value = world * args.steps / (ms / 1e3)
     names = ["transform", "gram", "reduce", "learn"]
     stage = {nm: float(np.mean([es[i].elapsed_time(es[i + 1]) for es in ev["stages"]])) for i, nm in enumerate(names)}
+    # the same step captured once into a CUDA graph (asynchronous entry points) and replayed
+    graph = None
+    if not args.no_graph:
+        from paper_2504_14338_gb300.graph import PipelineGraph
+        pg = PipelineGraph(Q, offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt, gram_mode=pipe_mode)
+        pg.capture()
+        for _ in range(args.warmup):
+            pg.replay()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            pg.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / args.steps
+        graph = {"ms_per_step": gms, "value": world / (gms / 1e3), "unit": UNIT,
+                 "flags": pg.flags_value(), "best_index": int(pg.res["best"].item())}
+        del pg
+        torch.cuda.empty_cache()
     gram_flops = w.n * w.k * (w.k + 1)
     gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
     modes = gram_modes_measure(dp, Q, last["D"], args.pipeline_gram, stage["gram"], ws) if rank == 0 else None
@@ -506,7 +527,7 @@ def main():
                 "gram_modes": modes, "learn_s": stage["learn"] / 1e3,
                 "best": {"index": best, "r": res.get("r"), "beta1": res.get("beta1"), "beta2": res.get("beta2")},
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
-                "clocks": ck, "split_gram": split, "learn_vs_sequential": seq}
+                "clocks": ck, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

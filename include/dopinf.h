@@ -48,6 +48,9 @@ enum dopinf_status {
 /* bits OR-ed into a device flag word */
 #define DOPINF_FLAG_NONFINITE 1u   /* NaN/Inf in the data */
 #define DOPINF_FLAG_ZERO_SCALE 2u  /* a variable block is constant after centering; scale := 1 */
+#define DOPINF_FLAG_TIMEOUT 4u     /* a bounded wait inside a kernel expired: outputs not valid */
+#define DOPINF_FLAG_RANK 8u        /* lambda_r <= 0, or the energy target not reached by r_cap */
+#define DOPINF_FLAG_NO_STABLE 16u  /* no (r, beta1, beta2) candidate is finite and bounded */
 
 enum dopinf_dtype { DOPINF_F64 = 0, DOPINF_F32 = 1 };
 
@@ -129,6 +132,12 @@ int64_t dopinf_tune_gram_chunk(int64_t rows);
 int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
                 int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
                 void* stream);
+/* The same product without any synchronisation (every mode; capturable into a CUDA graph):
+ * a bounded wait that expired inside a tensor-core kernel ORs DOPINF_FLAG_TIMEOUT into the
+ * device word *dev_flags (required) instead of returning DOPINF_E_TIMEOUT. */
+int dopinf_gram_async(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
+                      int accumulate, double* D, int64_t ldd, unsigned* dev_flags, void* ws,
+                      size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------
  * Allocation-free FP64 Gram.  The paper has no counterpart: this entry point exists for
@@ -175,6 +184,13 @@ size_t dopinf_reduce_workspace(int64_t k, int r_cap);
 int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed,
                   int r_cap, int* r_out, double* trace_out, double* eigvals, double* Tr,
                   double* Qhat, void* ws, size_t ws_bytes, void* stream);
+/* The same without synchronisation (capturable into a CUDA graph): r and trace(D) are written
+ * to the device words *r_dev and *trace_dev (r <= 0 where dopinf_reduce returns
+ * DOPINF_E_RANK: 0 = energy target not reached, -r = lambda_r <= 0), and the failures OR
+ * DOPINF_FLAG_RANK / DOPINF_FLAG_TIMEOUT into the device word *dev_flags (all required). */
+int dopinf_reduce_async(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed,
+                        int r_cap, int* r_dev, double* trace_dev, double* eigvals, double* Tr,
+                        double* Qhat, unsigned* dev_flags, void* ws, size_t ws_bytes, void* stream);
 /* Tuning of dopinf_reduce: 1 (default) reduces D to tridiagonal form in one cooperative
  * launch with a grid barrier per column (where 3 k doubles of shared memory fit, k <= 8533,
  * and the device supports cooperative launches); 0 uses three launches per column.  Both
@@ -215,6 +231,7 @@ int dopinf_tune_reduce_coop(int on);
  *            the stream) of the data matrices and normal equations, of the regularised
  *            solves, and of the rollouts.
  * Synchronises the stream.  Returns DOPINF_E_NO_STABLE if no candidate is valid.
+ * n_b1, n_b2 <= 64 (DOPINF_E_UNSUPPORTED above).
  * Workspace: dopinf_learn_workspace(...) bytes.
  * ------------------------------------------------------------------------------------ */
 /* Tuning of dopinf_learn: preferred CTAs (1, 2, 4 or 8) of the thread-block cluster that rolls
@@ -228,6 +245,17 @@ int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
                  int mode, double dt, int64_t n_steps, double max_growth, double* train_err,
                  double* growth, int* cand_status, int64_t* cand_steps, int* best_out,
                  double* O_best, double* stage_ms, void* ws, size_t ws_bytes, void* stream);
+
+/* The same without synchronisation and without host copies (capturable into a CUDA graph;
+ * the candidate tables are built on the device): best_dev (device int, required) receives the
+ * best index (-1 if none is valid, which also ORs DOPINF_FLAG_NO_STABLE into the device word
+ * *dev_flags, required), O_best receives its operators.  n_b1, n_b2 <= 64. */
+int dopinf_learn_async(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list,
+                       int n_r, const double* beta1, int n_b1, const double* beta2, int n_b2,
+                       int mode, double dt, int64_t n_steps, double max_growth, double* train_err,
+                       double* growth, int* cand_status, int64_t* cand_steps, int* best_dev,
+                       double* O_best, unsigned* dev_flags, void* ws, size_t ws_bytes,
+                       void* stream);
 
 /* ------------------------------------------------------------------------------------
  * Rollout of one quadratic ROM (eq. ROM_quad_time_discrete, or RK4 on

@@ -9,6 +9,28 @@ thread_local char g_last_error[256] = "";
 void set_last_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
 }
+
+namespace {
+__global__ void flag_if_set_kernel(const unsigned* err, unsigned* flags, unsigned bits) {
+  if (*err) atomicOr(flags, bits);
+}
+}  // namespace
+
+void flag_if_set(const unsigned* err, unsigned* flags, unsigned bits, cudaStream_t st) {
+  flag_if_set_kernel<<<1, 1, 0, st>>>(err, flags, bits);
+}
+
+int finish_timeout(const unsigned* err, unsigned* dev_flags, cudaStream_t st) {
+  if (dev_flags) {
+    flag_if_set(err, dev_flags, DOPINF_FLAG_TIMEOUT, st);
+    return launch_status();
+  }
+  unsigned e = 0;
+  DOPINF_CUDA(cudaMemcpyAsync(&e, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  DOPINF_CUDA(cudaStreamSynchronize(st));
+  if (e) set_last_error("a bounded wait inside a tensor-core kernel", cudaErrorTimeout);
+  return e ? DOPINF_E_TIMEOUT : DOPINF_OK;
+}
 }  // namespace dopinf
 
 DOPINF_API const char* dopinf_last_error(void) { return dopinf::g_last_error; }

@@ -47,6 +47,11 @@ inline int launch_status() {
   return DOPINF_E_CUDA;
 }
 
+// *flags |= bits if *err is non-zero (device-side status hand-off, no synchronisation).
+void flag_if_set(const unsigned* err, unsigned* flags, unsigned bits, cudaStream_t st);
+// Finish a call that left a device error word: flag it (asynchronous) or read it back.
+int finish_timeout(const unsigned* err, unsigned* dev_flags, cudaStream_t st);
+
 inline bool misaligned(const void* p, size_t a = kAlign) {
   return (reinterpret_cast<uintptr_t>(p) % a) != 0;
 }
@@ -75,10 +80,12 @@ size_t gram_tc_workspace(int64_t n, int64_t k);
 int64_t gram_tc_set_chunk_rows(int64_t rows);
 // FP64-accurate Gram from exact integer digit products on the tensor cores (gram_ozaki.cu).
 size_t gram_ozaki_workspace(int64_t n, int64_t k);
+// dev_flags == nullptr: synchronise and return DOPINF_E_TIMEOUT if a bounded wait expired;
+// otherwise stay asynchronous and OR DOPINF_FLAG_TIMEOUT into *dev_flags on the device.
 int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
-               void* ws, size_t ws_bytes, cudaStream_t st);
+               unsigned* dev_flags, void* ws, size_t ws_bytes, cudaStream_t st);
 int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
-            void* ws, size_t ws_bytes, cudaStream_t st);
+            unsigned* dev_flags, void* ws, size_t ws_bytes, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // Batched ROM rollouts (rollout.cu): one thread-block cluster per candidate.

@@ -629,17 +629,20 @@ DOPINF_API size_t dopinf_reduce_workspace(int64_t k, int r_cap) {
   return carve_reduce(nullptr, k, r_cap).used;
 }
 
-DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed, int r_cap,
-                             int* r_out, double* trace_out, double* eigvals, double* Tr, double* Qhat, void* ws,
-                             size_t ws_bytes, void* stream) {
-  if (!D || k < 1 || ldd < k || r_cap < 1 || r_cap > k || r_fixed > r_cap || !r_out || !trace_out || !eigvals ||
-      !Tr || !Qhat)
-    return DOPINF_E_ARG;
-  if (r_fixed <= 0 && !(energy_target >= 0.0 && energy_target < 1.0)) return DOPINF_E_ARG;
-  if (!ws || ws_bytes < dopinf_reduce_workspace(k, r_cap) || misaligned(ws)) return DOPINF_E_ARG;
-  if ((size_t)k * sizeof(double) > 200 * 1024) return DOPINF_E_UNSUPPORTED;  // back-transform keeps z in smem
-  cudaStream_t st = as_stream(stream);
-  ReduceWs w = carve_reduce(ws, k, r_cap);
+namespace dopinf {
+namespace {
+// r <= 0 (rank or energy failure) and an expired grid barrier as flag bits (asynchronous path).
+__global__ void reduce_flags(const int* r, const unsigned* bar_err, unsigned* flags) {
+  unsigned b = 0;
+  if (*r <= 0) b |= DOPINF_FLAG_RANK;
+  if (*bar_err) b |= DOPINF_FLAG_TIMEOUT;
+  if (b) atomicOr(flags, b);
+}
+
+// Everything but the read-back: r and trace(D) land in r_dev / trace_dev (device).
+int reduce_launch(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed, int r_cap,
+                  int* r_dev, double* trace_dev, double* eigvals, double* Tr, double* Qhat, const ReduceWs& w,
+                  cudaStream_t st) {
   DOPINF_CUDA(cudaMemcpy2DAsync(w.A, k * sizeof(double), D, ldd * sizeof(double), k * sizeof(double), k,
                                 cudaMemcpyDeviceToDevice, st));
   DOPINF_TRY(tridiagonalise(w, k, st));
@@ -653,8 +656,42 @@ DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double ene
   hh_back<<<r_cap, EB, smem, st>>>(w.A, k, r_cap, w.tau, w.lam, w.Z, w.U, Tr);
   DOPINF_TRY(launch_status());
   DOPINF_TRY(tn_product(Tr, k, D, ldd, DOPINF_F64, k, r_cap, k, 0, 0, Qhat, r_cap, w.tn, w.tn_bytes, st));
-  finalize_rank<<<1, 32, 0, st>>>(D, k, ldd, w.lam, r_cap, energy_target, r_fixed, eigvals, w.r, w.trace);
-  DOPINF_TRY(launch_status());
+  finalize_rank<<<1, 32, 0, st>>>(D, k, ldd, w.lam, r_cap, energy_target, r_fixed, eigvals, r_dev, trace_dev);
+  return launch_status();
+}
+
+int reduce_check(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed, int r_cap,
+                 const double* eigvals, const double* Tr, const double* Qhat, void* ws, size_t ws_bytes) {
+  if (!D || k < 1 || ldd < k || r_cap < 1 || r_cap > k || r_fixed > r_cap || !eigvals || !Tr || !Qhat)
+    return DOPINF_E_ARG;
+  if (r_fixed <= 0 && !(energy_target >= 0.0 && energy_target < 1.0)) return DOPINF_E_ARG;
+  if (!ws || ws_bytes < dopinf_reduce_workspace(k, r_cap) || misaligned(ws)) return DOPINF_E_ARG;
+  if ((size_t)k * sizeof(double) > 200 * 1024) return DOPINF_E_UNSUPPORTED;  // back-transform keeps z in smem
+  return DOPINF_OK;
+}
+}  // namespace
+}  // namespace dopinf
+
+DOPINF_API int dopinf_reduce_async(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed,
+                                   int r_cap, int* r_dev, double* trace_dev, double* eigvals, double* Tr,
+                                   double* Qhat, unsigned* dev_flags, void* ws, size_t ws_bytes, void* stream) {
+  if (!r_dev || !trace_dev || !dev_flags) return DOPINF_E_ARG;
+  DOPINF_TRY(reduce_check(D, k, ldd, energy_target, r_fixed, r_cap, eigvals, Tr, Qhat, ws, ws_bytes));
+  cudaStream_t st = as_stream(stream);
+  ReduceWs w = carve_reduce(ws, k, r_cap);
+  DOPINF_TRY(reduce_launch(D, k, ldd, energy_target, r_fixed, r_cap, r_dev, trace_dev, eigvals, Tr, Qhat, w, st));
+  reduce_flags<<<1, 1, 0, st>>>(r_dev, &w.bar->err, dev_flags);
+  return launch_status();
+}
+
+DOPINF_API int dopinf_reduce(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed, int r_cap,
+                             int* r_out, double* trace_out, double* eigvals, double* Tr, double* Qhat, void* ws,
+                             size_t ws_bytes, void* stream) {
+  if (!r_out || !trace_out) return DOPINF_E_ARG;
+  DOPINF_TRY(reduce_check(D, k, ldd, energy_target, r_fixed, r_cap, eigvals, Tr, Qhat, ws, ws_bytes));
+  cudaStream_t st = as_stream(stream);
+  ReduceWs w = carve_reduce(ws, k, r_cap);
+  DOPINF_TRY(reduce_launch(D, k, ldd, energy_target, r_fixed, r_cap, w.r, w.trace, eigvals, Tr, Qhat, w, st));
   int r_host = 0;
   double tr_host = 0.0;
   DOPINF_CUDA(cudaMemcpyAsync(&r_host, w.r, sizeof(int), cudaMemcpyDeviceToHost, st));

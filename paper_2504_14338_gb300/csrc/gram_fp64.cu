@@ -195,9 +195,8 @@ DOPINF_API size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mod
   return tn_workspace(n, k, k, 1);
 }
 
-DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
-                           int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
-                           void* stream) {
+static int gram_impl(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode, int accumulate,
+                     double* D, int64_t ldd, unsigned* dev_flags, void* ws, size_t ws_bytes, void* stream) {
   if (n < 0 || k < 1 || ldq < (n > 1 ? n : 1) || ldd < k || !D || (n > 0 && !Q)) return DOPINF_E_ARG;
   if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
   if (mode != DOPINF_GRAM_FP64 && mode != DOPINF_GRAM_BF16X4 && mode != DOPINF_GRAM_OZAKI_FP64)
@@ -207,10 +206,24 @@ DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64
     return cuda_status(cudaMemset2DAsync(D, ldd * sizeof(double), 0, k * sizeof(double), k,
                                          as_stream(stream)));
   }
-  if (mode == DOPINF_GRAM_BF16X4) return gram_tc(Q, dtype, n, k, ldq, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
+  if (mode == DOPINF_GRAM_BF16X4)
+    return gram_tc(Q, dtype, n, k, ldq, accumulate, D, ldd, dev_flags, ws, ws_bytes, as_stream(stream));
   if (mode == DOPINF_GRAM_OZAKI_FP64)
-    return gram_ozaki(Q, dtype, n, k, ldq, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
+    return gram_ozaki(Q, dtype, n, k, ldq, accumulate, D, ldd, dev_flags, ws, ws_bytes, as_stream(stream));
   return tn_product(Q, ldq, Q, ldq, dtype, n, k, k, 1, accumulate, D, ldd, ws, ws_bytes, as_stream(stream));
+}
+
+DOPINF_API int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
+                           int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
+                           void* stream) {
+  return gram_impl(Q, dtype, n, k, ldq, mode, accumulate, D, ldd, nullptr, ws, ws_bytes, stream);
+}
+
+DOPINF_API int dopinf_gram_async(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
+                                 int accumulate, double* D, int64_t ldd, unsigned* dev_flags, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  if (!dev_flags) return DOPINF_E_ARG;
+  return gram_impl(Q, dtype, n, k, ldq, mode, accumulate, D, ldd, dev_flags, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -506,7 +506,7 @@ OzWs carve_oz(void* base, int64_t n, int64_t k) {
 size_t gram_ozaki_workspace(int64_t n, int64_t k) { return carve_oz(nullptr, n, k).used; }
 
 int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
-               void* ws, size_t ws_bytes, cudaStream_t st) {
+               unsigned* dev_flags, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (k > 65535 || n > ((int64_t)1 << 40)) return DOPINF_E_UNSUPPORTED;
   const OzShape sh = make_oz_shape(n, k);
   if ((int64_t)NDIG * sh.nrb * sh.ncb > (int64_t)INT32_MAX) return DOPINF_E_UNSUPPORTED;
@@ -556,10 +556,7 @@ int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
   const int64_t kk = k * k;
   ozaki_reduce<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(w.part, sh, w.sexp, accumulate, D, ldd);
   DOPINF_TRY(launch_status());
-  unsigned e = 0;
-  DOPINF_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  DOPINF_CUDA(cudaStreamSynchronize(st));
-  return e ? DOPINF_E_TIMEOUT : DOPINF_OK;
+  return finish_timeout(w.err, dev_flags, st);
 }
 
 }  // namespace dopinf

@@ -423,7 +423,7 @@ int64_t gram_tc_set_chunk_rows(int64_t rows) {
 }
 
 int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
-            void* ws, size_t ws_bytes, cudaStream_t st) {
+            unsigned* dev_flags, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (n > ((int64_t)1 << 31) - BK || k > 65535) return DOPINF_E_UNSUPPORTED;
   if (((n + BK - 1) / BK) * ((k + BM - 1) / BM) > (int64_t)INT32_MAX) return DOPINF_E_UNSUPPORTED;
   if (!ws || ws_bytes < gram_tc_workspace(n, k) || misaligned(ws)) return DOPINF_E_ARG;
@@ -454,10 +454,7 @@ int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int acc
   const int64_t kk = k * k;
   gram_tc_reduce<<<(unsigned)((kk + 255) / 256), 256, 0, st>>>(w.part, sh, accumulate, D, ldd);
   DOPINF_TRY(launch_status());
-  unsigned e = 0;
-  DOPINF_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  DOPINF_CUDA(cudaStreamSynchronize(st));
-  return e ? DOPINF_E_TIMEOUT : DOPINF_OK;
+  return finish_timeout(w.err, dev_flags, st);
 }
 
 }  // namespace dopinf

@@ -89,7 +89,7 @@ __global__ void select_best(const double* err, const int* status, int n_cand, in
   *best = b;
 }
 
-inline int dim_d(int r) { return r + r * (r + 1) / 2 + 1; }
+__host__ __device__ inline int dim_d(int r) { return r + r * (r + 1) / 2 + 1; }
 
 constexpr int kMaxR = 64;  // entries of the r list
 
@@ -169,23 +169,99 @@ DOPINF_API size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list
   return carve_learn(nullptr, k - 1, r_list, n_r, n_b1, n_b2).used;
 }
 
-DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
-                            const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt,
-                            int64_t n_steps, double max_growth, double* train_err, double* growth, int* cand_status,
-                            int64_t* cand_steps, int* best_out, double* O_best, double* stage_ms, void* ws,
-                            size_t ws_bytes, void* stream) {
+namespace dopinf {
+namespace {
+
+constexpr int kMaxB = 64;  // entries of each beta list
+
+// The grid as kernel parameters, so that the candidate tables are built on the device (no host
+// copies: the launch sequence can be captured into a CUDA graph).
+struct LearnGrid {
+  int n_r, n_b1, n_b2;
+  int r_list[kMaxR];
+  double beta1[kMaxB], beta2[kMaxB];
+  LearnWs w;
+};
+
+__global__ void build_tables(const LearnGrid g) {
+  const int n_pairs = g.n_b1 * g.n_b2;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < g.n_r * g.n_b2; u += gridDim.x * blockDim.x) {
+    const int ir = u / g.n_b2, i2 = u % g.n_b2;
+    const int r = g.r_list[ir], sq = r * (r + 1) / 2;
+    SchurUnit U;
+    U.G = g.w.G[ir];
+    U.B = g.w.B[ir];
+    U.E = g.w.E[ir] + (size_t)i2 * ((size_t)(sq + 2 * r + 1) * (sq + 2 * r + 1));
+    U.b2 = g.beta2[i2];
+    U.r = r;
+    U.d = dim_d(r);
+    U.s = sq;
+    U.m = r + 1;
+    U.N = sq + 2 * r + 1;
+    U.unit = u;
+    g.w.units[u] = U;
+  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_r * n_pairs; c += gridDim.x * blockDim.x) {
+    const int ir = c / n_pairs, p = c % n_pairs, i2 = p % g.n_b2;
+    const int r = g.r_list[ir], d = dim_d(r), sq = r * (r + 1) / 2, N = sq + 2 * r + 1;
+    SchurCand S;
+    S.E = g.w.E[ir] + (size_t)i2 * ((size_t)N * N);
+    S.O = g.w.O[ir] + (size_t)p * r * d;
+    S.scratch = g.w.S[ir] + (size_t)p * ((size_t)(r + 1) * (r + 1) + (size_t)(r + 1) * r);
+    S.b1 = g.beta1[p / g.n_b2];
+    S.r = r;
+    S.s = sq;
+    S.m = r + 1;
+    S.N = N;
+    S.unit = ir * g.n_b2 + i2;
+    S.cand = c;
+    g.w.cands[c] = S;
+    RolloutCand R;
+    R.O = S.O;
+    R.ldo = r;
+    R.r = r;
+    R.d = d;
+    R.cand = c;
+    R.mu = g.w.mu + (size_t)ir * g.w.r_stride;
+    R.denom = g.w.denom + ir;
+    g.w.roll[c] = R;
+  }
+}
+
+// The operators of the best candidate into O_best (r_max x d_max, ld r_max); best < 0 flags
+// DOPINF_FLAG_NO_STABLE.  The candidate's r and d come from the table.
+__global__ void gather_best(const int* best, const SchurCand* cands, int r_max, double* O_best, int* best_out,
+                            unsigned* flags) {
+  const int b = *best;
+  if (threadIdx.x == 0 && best_out) *best_out = b;
+  if (b < 0) {
+    if (threadIdx.x == 0 && flags) atomicOr(flags, DOPINF_FLAG_NO_STABLE);
+    return;
+  }
+  const SchurCand c = cands[b];
+  const int r = c.r, d = dim_d(r);
+  for (int e = threadIdx.x; e < r * d; e += blockDim.x) O_best[(e % r) + (size_t)(e / r) * r_max] = c.O[e];
+}
+
+// Checks of every argument; the rollout cluster size on success.
+int learn_check(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
+                const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt, int64_t n_steps,
+                double max_growth, const double* train_err, const double* growth, const int* cand_status,
+                const double* O_best, void* ws, size_t ws_bytes, int* cluster, int* r_used, int* d_max) {
   if (!Qhat || r_max < 1 || ldqh < r_max || !r_list || n_r < 1 || n_r > kMaxR || !beta1 || !beta2 || n_b1 < 1 ||
-      n_b2 < 1 || !train_err || !growth || !cand_status || !best_out || !O_best)
+      n_b2 < 1 || !train_err || !growth || !cand_status || !O_best)
     return DOPINF_E_ARG;
+  if (n_b1 > kMaxB || n_b2 > kMaxB) return DOPINF_E_UNSUPPORTED;
   if (mode != DOPINF_DISCRETE && mode != DOPINF_CONTINUOUS_RK4) return DOPINF_E_ARG;
   if (mode == DOPINF_CONTINUOUS_RK4 && !(dt > 0.0)) return DOPINF_E_ARG;
   const int64_t K = learn_rows(k, mode);
   if (K < 1 || n_steps < k || !(max_growth > 0.0)) return DOPINF_E_ARG;
-  int d_max = 0, r_used = 0;
+  *d_max = 0;
+  *r_used = 0;
   for (int i = 0; i < n_r; ++i) {
     if (r_list[i] < 1 || r_list[i] > r_max || r_list[i] > 255) return DOPINF_E_ARG;
-    d_max = dim_d(r_list[i]) > d_max ? dim_d(r_list[i]) : d_max;
-    r_used = r_list[i] > r_used ? r_list[i] : r_used;
+    *d_max = dim_d(r_list[i]) > *d_max ? dim_d(r_list[i]) : *d_max;
+    *r_used = r_list[i] > *r_used ? r_list[i] : *r_used;
   }
   for (int i = 0; i < n_b1; ++i)
     if (!(beta1[i] >= 0.0)) return DOPINF_E_ARG;
@@ -193,74 +269,42 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     if (!(beta2[i] >= 0.0)) return DOPINF_E_ARG;
   if (!ws || ws_bytes < dopinf_learn_workspace(r_max, k, r_list, n_r, n_b1, n_b2) || misaligned(ws))
     return DOPINF_E_ARG;
-  const int cluster = rollout_cluster_size(r_used, d_max, r_used >= 16 ? g_cluster_want : 1);
-  if (!cluster) return DOPINF_E_UNSUPPORTED;
-  cudaStream_t st = as_stream(stream);
+  *cluster = rollout_cluster_size(*r_used, *d_max, *r_used >= 16 ? g_cluster_want : 1);
+  return *cluster ? DOPINF_OK : DOPINF_E_UNSUPPORTED;
+}
+
+// The whole learn step on the stream, no synchronisation, no host copies.  ev (optional): 4
+// events recorded around the data + normal equations, the solves and the rollouts.
+int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
+                 const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt, int64_t n_steps,
+                 double max_growth, double* train_err, double* growth, int* cand_status, int64_t* cand_steps,
+                 int* best_dev, double* O_best, unsigned* dev_flags, int cluster, int r_used, int d_max, void* ws,
+                 cudaStream_t st, cudaEvent_t* ev) {
+  const int64_t K = learn_rows(k, mode);
   // the workspace is laid out for K = k - 1 rows, which covers both modes
   LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1, n_b2);
-  const int n_pairs = n_b1 * n_b2, n_cand = n_r * n_pairs;
-  // candidate tables, built on the host: c = (ir * n_b1 + i1) * n_b2 + i2; unit = ir * n_b2 + i2
-  const int n_units = n_r * n_b2;
+  const int n_pairs = n_b1 * n_b2, n_cand = n_r * n_pairs, n_units = n_r * n_b2;
+  // candidate c = (ir * n_b1 + i1) * n_b2 + i2; unit = ir * n_b2 + i2
+  LearnGrid g;
+  g.n_r = n_r;
+  g.n_b1 = n_b1;
+  g.n_b2 = n_b2;
+  for (int i = 0; i < n_r; ++i) g.r_list[i] = r_list[i];
+  for (int i = 0; i < n_b1; ++i) g.beta1[i] = beta1[i];
+  for (int i = 0; i < n_b2; ++i) g.beta2[i] = beta2[i];
+  g.w = w;
+  build_tables<<<(n_cand + 255) / 256, 256, 0, st>>>(g);
+  DOPINF_TRY(launch_status());
+  // the unit table's sizes on the host too: they set the grids of the panel launches
   std::vector<SchurUnit> un(n_units);
-  SchurCand* ch = new SchurCand[n_cand];
-  RolloutCand* ro = new RolloutCand[n_cand];
-  for (int ir = 0; ir < n_r; ++ir) {
-    const int r = r_list[ir], d = dim_d(r), sq = r * (r + 1) / 2, N = sq + 2 * r + 1;
-    for (int i2 = 0; i2 < n_b2; ++i2) {
-      SchurUnit& U = un[ir * n_b2 + i2];
-      U.G = w.G[ir];
-      U.B = w.B[ir];
-      U.E = w.E[ir] + (size_t)i2 * schur_unit_doubles(r);
-      U.b2 = beta2[i2];
-      U.r = r;
-      U.d = d;
-      U.s = sq;
-      U.m = r + 1;
-      U.N = N;
-      U.unit = ir * n_b2 + i2;
-    }
-    for (int p = 0; p < n_pairs; ++p) {
-      const int c = ir * n_pairs + p, i2 = p % n_b2;
-      ch[c].E = un[ir * n_b2 + i2].E;
-      ch[c].O = w.O[ir] + (size_t)p * r * d;
-      ch[c].scratch = w.S[ir] + (size_t)p * schur_cand_doubles(r);
-      ch[c].b1 = beta1[p / n_b2];
-      ch[c].r = r;
-      ch[c].s = sq;
-      ch[c].m = r + 1;
-      ch[c].N = N;
-      ch[c].unit = ir * n_b2 + i2;
-      ch[c].cand = c;
-      ro[c].O = ch[c].O;
-      ro[c].ldo = r;
-      ro[c].r = r;
-      ro[c].d = d;
-      ro[c].cand = c;
-      ro[c].mu = w.mu + (size_t)ir * w.r_stride;
-      ro[c].denom = w.denom + ir;
-    }
+  for (int u = 0; u < n_units; ++u) {
+    const int r = r_list[u / n_b2], sq = r * (r + 1) / 2;
+    un[u].r = r;
+    un[u].s = sq;
+    un[u].m = r + 1;
+    un[u].N = sq + 2 * r + 1;
   }
-  // pageable host -> device copies: the runtime stages the source before returning
-  cudaError_t e0 = cudaMemcpyAsync(w.units, un.data(), sizeof(SchurUnit) * n_units, cudaMemcpyHostToDevice, st);
-  cudaError_t e1 = cudaMemcpyAsync(w.cands, ch, sizeof(SchurCand) * n_cand, cudaMemcpyHostToDevice, st);
-  cudaError_t e2 = cudaMemcpyAsync(w.roll, ro, sizeof(RolloutCand) * n_cand, cudaMemcpyHostToDevice, st);
-  delete[] ch;
-  delete[] ro;
-  DOPINF_CUDA(e0);
-  DOPINF_CUDA(e1);
-  DOPINF_CUDA(e2);
-  // optional stage timings (CUDA events on this stream): data + normal equations, solves, rollouts
-  cudaEvent_t ev[4] = {};
-  if (stage_ms)
-    for (int i = 0; i < 4; ++i) DOPINF_CUDA(cudaEventCreate(&ev[i]));
-  struct EvGuard {
-    cudaEvent_t* e;
-    ~EvGuard() {
-      for (int i = 0; i < 4; ++i)
-        if (e[i]) cudaEventDestroy(e[i]);
-    }
-  } ev_guard{ev};
-  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[0], st));
+  if (ev) DOPINF_CUDA(cudaEventRecord(ev[0], st));
   const int64_t t0 = mode == DOPINF_DISCRETE ? 0 : 1;
   for (int ir = 0; ir < n_r; ++ir) {
     const int r = r_list[ir], d = dim_d(r);
@@ -273,9 +317,9 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * w.r_stride, w.denom + ir);
     DOPINF_TRY(launch_status());
   }
-  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[1], st));
+  if (ev) DOPINF_CUDA(cudaEventRecord(ev[1], st));
   DOPINF_TRY(schur_solve(w.units, un.data(), n_units, w.cands, n_cand, w.unit_fail, cand_status, st));
-  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[2], st));
+  if (ev) DOPINF_CUDA(cudaEventRecord(ev[2], st));
   RolloutBatch bt = {};
   bt.cands = w.roll;
   bt.n_cand = n_cand;
@@ -295,9 +339,54 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
   bt.status = cand_status;
   bt.steps = cand_steps;
   DOPINF_TRY(launch_rollouts(bt, cluster, st));
-  if (stage_ms) DOPINF_CUDA(cudaEventRecord(ev[3], st));
+  if (ev) DOPINF_CUDA(cudaEventRecord(ev[3], st));
   select_best<<<1, 32, 0, st>>>(train_err, cand_status, n_cand, w.best);
-  DOPINF_TRY(launch_status());
+  gather_best<<<1, 256, 0, st>>>(w.best, w.cands, r_max, O_best, best_dev, dev_flags);
+  return launch_status();
+}
+
+}  // namespace
+}  // namespace dopinf
+
+DOPINF_API int dopinf_learn_async(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
+                                  const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt,
+                                  int64_t n_steps, double max_growth, double* train_err, double* growth,
+                                  int* cand_status, int64_t* cand_steps, int* best_dev, double* O_best,
+                                  unsigned* dev_flags, void* ws, size_t ws_bytes, void* stream) {
+  if (!best_dev || !dev_flags) return DOPINF_E_ARG;
+  int cluster = 0, r_used = 0, d_max = 0;
+  DOPINF_TRY(learn_check(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
+                         train_err, growth, cand_status, O_best, ws, ws_bytes, &cluster, &r_used, &d_max));
+  return learn_launch(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
+                      train_err, growth, cand_status, cand_steps, best_dev, O_best, dev_flags, cluster, r_used, d_max,
+                      ws, as_stream(stream), nullptr);
+}
+
+DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
+                            const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt,
+                            int64_t n_steps, double max_growth, double* train_err, double* growth, int* cand_status,
+                            int64_t* cand_steps, int* best_out, double* O_best, double* stage_ms, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!best_out) return DOPINF_E_ARG;
+  int cluster = 0, r_used = 0, d_max = 0;
+  DOPINF_TRY(learn_check(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
+                         train_err, growth, cand_status, O_best, ws, ws_bytes, &cluster, &r_used, &d_max));
+  cudaStream_t st = as_stream(stream);
+  // optional stage timings (CUDA events on this stream): data + normal equations, solves, rollouts
+  cudaEvent_t ev[4] = {};
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } ev_guard{ev};
+  if (stage_ms)
+    for (int i = 0; i < 4; ++i) DOPINF_CUDA(cudaEventCreate(&ev[i]));
+  LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1, n_b2);
+  DOPINF_TRY(learn_launch(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
+                          train_err, growth, cand_status, cand_steps, nullptr, O_best, nullptr, cluster, r_used, d_max,
+                          ws, st, stage_ms ? ev : nullptr));
   int best = -1;
   DOPINF_CUDA(cudaMemcpyAsync(&best, w.best, sizeof(int), cudaMemcpyDeviceToHost, st));
   DOPINF_CUDA(cudaStreamSynchronize(st));
@@ -308,13 +397,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
       DOPINF_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
       stage_ms[i] = ms;
     }
-  if (best < 0) return DOPINF_E_NO_STABLE;
-  const int ir = best / n_pairs, p = best % n_pairs, r = r_list[ir], d = dim_d(r);
-  const double* src = w.O[ir] + (size_t)p * r * d;
-  DOPINF_CUDA(cudaMemcpy2DAsync(O_best, sizeof(double) * r_max, src, sizeof(double) * r, sizeof(double) * r, d,
-                                cudaMemcpyDeviceToDevice, st));
-  DOPINF_CUDA(cudaStreamSynchronize(st));
-  return DOPINF_OK;
+  return best < 0 ? DOPINF_E_NO_STABLE : DOPINF_OK;
 }
 
 DOPINF_API int dopinf_tune_learn_cluster(int cluster) { return learn_set_cluster(cluster); }

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdopinf.so")
 
 OK, E_ARG, E_CUDA, E_NONFINITE, E_RANK, E_NO_STABLE, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -4, -6, -7, -8, -9
-FLAG_NONFINITE, FLAG_ZERO_SCALE = 1, 2
+FLAG_NONFINITE, FLAG_ZERO_SCALE, FLAG_TIMEOUT, FLAG_RANK, FLAG_NO_STABLE = 1, 2, 4, 8, 16
 F64, F32 = 0, 1
 CENTER, SCALE = 1, 2
 GRAM_FP64, GRAM_BF16X4, GRAM_OZAKI_FP64 = 0, 1, 2
@@ -52,6 +52,15 @@ def _load():
         "dopinf_gram_workspace": (_c_sz, [_c_i64, _c_i64, ctypes.c_int, ctypes.c_int]),
         "dopinf_gram": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int,
                                        ctypes.c_int, _c_p, _c_i64, _c_p, _c_sz, _c_p]),
+        "dopinf_gram_async": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int,
+                                             ctypes.c_int, _c_p, _c_i64, _c_p, _c_p, _c_sz, _c_p]),
+        "dopinf_reduce_async": (ctypes.c_int, [_c_p, _c_i64, _c_i64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                               _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
+        "dopinf_learn_async": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, _c_i64, ctypes.c_double, _c_p, _c_p, _c_p, _c_p,
+                                              _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p]),
         "dopinf_reduce_workspace": (_c_sz, [_c_i64, ctypes.c_int]),
         "dopinf_reduce": (ctypes.c_int, [_c_p, _c_i64, _c_i64, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -183,6 +192,18 @@ def dopinf_gram(Q, mode=GRAM_FP64, D=None, accumulate=False, ws=None, stream=Non
     return D
 
 
+def dopinf_gram_async(Q, D, flags, mode=GRAM_FP64, accumulate=False, ws=None, stream=None):
+    """dopinf_gram without synchronisation (capturable): a kernel timeout ORs FLAG_TIMEOUT into
+    the device word `flags` (int32 tensor of one element)."""
+    n, k, ldq = _colmajor(Q)
+    nb = lib.dopinf_gram_workspace(n, k, _dtype_code(Q), mode)
+    buf, nb = _ws(nb, ws, Q.device)
+    _check("dopinf_gram_async", lib.dopinf_gram_async(_ptr(Q), _dtype_code(Q), n, k, ldq, mode, int(accumulate),
+                                                      _ptr(D), D.stride(0), _ptr(flags), _ptr(buf), nb,
+                                                      _stream(stream)))
+    return D
+
+
 def dopinf_tune_gram_chunk(rows=0):
     """Sets (rows > 0) or queries the FP32 accumulation chunk of the split Gram; returns the previous value."""
     return int(lib.dopinf_tune_gram_chunk(int(rows)))
@@ -218,6 +239,41 @@ def dopinf_reduce(D, r_cap, energy_target=0.9996, r_fixed=0, ws=None, stream=Non
                            _stream(stream))
     _check("dopinf_reduce", st)
     return dict(r=r.value, trace=tr.value, eigvals=eig, Tr=Tr, Qhat=Qhat, status=st)
+
+
+def dopinf_reduce_async(D, r_cap, out, energy_target=0.9996, r_fixed=0, ws=None, stream=None):
+    """dopinf_reduce without synchronisation (capturable).  `out` holds preallocated device
+    tensors: eigvals (r_cap), Tr (k x r_cap column-major), Qhat (r_cap x k column-major),
+    r (int32, 1), trace (float64, 1), flags (int32, 1)."""
+    k = D.shape[0]
+    nb = lib.dopinf_reduce_workspace(k, r_cap)
+    buf, nb = _ws(nb, ws, D.device)
+    _check("dopinf_reduce_async",
+           lib.dopinf_reduce_async(_ptr(D), k, D.stride(0), float(energy_target), int(r_fixed), int(r_cap),
+                                   _ptr(out["r"]), _ptr(out["trace"]), _ptr(out["eigvals"]), _ptr(out["Tr"]),
+                                   _ptr(out["Qhat"]), _ptr(out["flags"]), _ptr(buf), nb, _stream(stream)))
+    return out
+
+
+def dopinf_learn_async(Qhat, r_list, beta1, beta2, n_steps, out, mode=DISCRETE, dt=1.0, max_growth=1.2, ws=None,
+                       stream=None):
+    """dopinf_learn without synchronisation (capturable).  `out` holds preallocated device
+    tensors: train_err, growth (float64, n_cand), status (int32, n_cand), steps (int64,
+    n_cand), best (int32, 1), O_best (r_max x d_max column-major), flags (int32, 1)."""
+    r_max, k = Qhat.shape
+    rl = (ctypes.c_int * len(r_list))(*[int(r) for r in r_list])
+    b1 = (ctypes.c_double * len(beta1))(*[float(b) for b in beta1])
+    b2 = (ctypes.c_double * len(beta2))(*[float(b) for b in beta2])
+    nb = lib.dopinf_learn_workspace(r_max, k, rl, len(r_list), len(beta1), len(beta2))
+    buf, nb = _ws(nb, ws, Qhat.device)
+    O = out["O_best"]
+    _check("dopinf_learn_async",
+           lib.dopinf_learn_async(_ptr(Qhat), r_max, k, Qhat.stride(1), rl, len(r_list), b1, len(beta1), b2,
+                                  len(beta2), int(mode), float(dt), int(n_steps), float(max_growth),
+                                  _ptr(out["train_err"]), _ptr(out["growth"]), _ptr(out["status"]),
+                                  _ptr(out["steps"]), _ptr(out["best"]), _ptr(O), _ptr(out["flags"]), _ptr(buf),
+                                  nb, _stream(stream)))
+    return out
 
 
 def dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=DISCRETE, dt=1.0, max_growth=1.2, ws=None,

@@ -1,0 +1,108 @@
+"""The whole hot path (Steps II-IV) captured once into a CUDA graph and replayed.
+
+Every buffer is allocated up front; capture records the asynchronous entry points
+(dopinf_transform, dopinf_gram_async, dopinf_reduce_async, dopinf_learn_async), which neither
+synchronise nor copy from the host, so a replay reruns the transform, the Gram, the eigensolve
+and projection, the regularised solves, the rollouts and the selection with one launch from
+the host.  Failures (a kernel timeout, a rank failure, no valid candidate) are OR-ed into one
+device flag word that the caller reads when it wants to.
+"""
+import ctypes
+
+import torch
+
+from . import dopinf as dp
+
+
+class PipelineGraph:
+    def __init__(self, Q, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0,
+                 gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2):
+        self.Q = Q
+        n, k, ldq = dp._colmajor(Q)
+        dev = Q.device
+        self.n, self.k, self.ldq = n, k, ldq
+        self.offs = (dp._c_i64 * len(var_row_offsets))(*[int(v) for v in var_row_offsets])
+        self.n_vars = len(var_row_offsets) - 1
+        self.r_cap = int(r_cap)
+        self.r_fixed = int(r_cap if r_fixed is None else r_fixed)
+        self.energy_target = float(energy_target)
+        self.gram_mode = gram_mode
+        self.r_list = [int(r) for r in r_list]
+        self.beta1 = [float(b) for b in beta1]
+        self.beta2 = [float(b) for b in beta2]
+        self.n_steps, self.mode, self.dt, self.max_growth = int(n_steps), int(mode), float(dt), float(max_growth)
+        f64, i32 = torch.float64, torch.int32
+        self.flags = torch.zeros(1, dtype=i32, device=dev)
+        self.mean = torch.empty(n, dtype=f64, device=dev)
+        self.scale = torch.empty(self.n_vars, dtype=f64, device=dev)
+        self.D = torch.zeros(k, k, dtype=f64, device=dev)
+        self.red = dict(eigvals=torch.empty(r_cap, dtype=f64, device=dev),
+                        Tr=torch.empty(r_cap, k, dtype=f64, device=dev).t(),
+                        Qhat=torch.empty(k, r_cap, dtype=f64, device=dev).t(),
+                        r=torch.zeros(1, dtype=i32, device=dev), trace=torch.zeros(1, dtype=f64, device=dev))
+        n_cand = len(self.r_list) * len(self.beta1) * len(self.beta2)
+        d_max = max(r + r * (r + 1) // 2 + 1 for r in self.r_list)
+        self.res = dict(train_err=torch.empty(n_cand, dtype=f64, device=dev),
+                        growth=torch.empty(n_cand, dtype=f64, device=dev),
+                        status=torch.empty(n_cand, dtype=i32, device=dev),
+                        steps=torch.zeros(n_cand, dtype=torch.int64, device=dev),
+                        best=torch.zeros(1, dtype=i32, device=dev),
+                        O_best=torch.zeros(d_max, r_cap, dtype=f64, device=dev).t())
+        # one workspace per stage, sized before capture
+        rl = (ctypes.c_int * len(self.r_list))(*self.r_list)
+        sizes = [dp.lib.dopinf_transform_workspace(n, self.n_vars),
+                 dp.lib.dopinf_gram_workspace(n, k, dp._dtype_code(Q), gram_mode),
+                 dp.lib.dopinf_reduce_workspace(k, r_cap),
+                 dp.lib.dopinf_learn_workspace(r_cap, k, rl, len(self.r_list), len(self.beta1), len(self.beta2))]
+        self.ws = [dp.Workspace(dev) for _ in sizes]
+        self.wbuf = [w.get(nb) for w, nb in zip(self.ws, sizes)]
+        self.wsz = sizes
+        self.graph = None
+
+    def _launch(self, stream):
+        """The pipeline on `stream` through the asynchronous entry points (no host synchronisation)."""
+        L, P, s = dp.lib, dp._ptr, dp._stream(stream)
+        red, res = self.red, self.res
+        dp._check("dopinf_transform", L.dopinf_transform(
+            P(self.Q), dp._dtype_code(self.Q), self.n, self.k, self.ldq, self.n_vars, self.offs,
+            dp.CENTER | dp.SCALE, P(self.mean), P(self.scale), P(self.flags), P(self.wbuf[0]), self.wsz[0], s))
+        dp._check("dopinf_gram_async", L.dopinf_gram_async(
+            P(self.Q), dp._dtype_code(self.Q), self.n, self.k, self.ldq, self.gram_mode, 0, P(self.D),
+            self.D.stride(0), P(self.flags), P(self.wbuf[1]), self.wsz[1], s))
+        dp._check("dopinf_reduce_async", L.dopinf_reduce_async(
+            P(self.D), self.k, self.D.stride(0), self.energy_target, self.r_fixed, self.r_cap, P(red["r"]),
+            P(red["trace"]), P(red["eigvals"]), P(red["Tr"]), P(red["Qhat"]), P(self.flags), P(self.wbuf[2]),
+            self.wsz[2], s))
+        rl = (ctypes.c_int * len(self.r_list))(*self.r_list)
+        b1 = (ctypes.c_double * len(self.beta1))(*self.beta1)
+        b2 = (ctypes.c_double * len(self.beta2))(*self.beta2)
+        Qh = red["Qhat"]
+        dp._check("dopinf_learn_async", L.dopinf_learn_async(
+            P(Qh), self.r_cap, self.k, Qh.stride(1), rl, len(self.r_list), b1, len(self.beta1), b2,
+            len(self.beta2), self.mode, self.dt, self.n_steps, self.max_growth, P(res["train_err"]),
+            P(res["growth"]), P(res["status"]), P(res["steps"]), P(res["best"]), P(res["O_best"]),
+            P(self.flags), P(self.wbuf[3]), self.wsz[3], s))
+
+    def run_eager(self, stream=None):
+        """One pass without the graph (the same launches, issued from the host)."""
+        self._launch(stream if stream is not None else torch.cuda.current_stream())
+
+    def capture(self):
+        """Capture the pipeline into a CUDA graph (after one eager warm-up pass)."""
+        side = torch.cuda.Stream(device=self.Q.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._launch(side)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._launch(torch.cuda.current_stream())
+        return self
+
+    def replay(self):
+        self.graph.replay()
+
+    def flags_value(self):
+        """The OR of the DOPINF_FLAG_* bits raised so far (synchronises)."""
+        return int(self.flags.item())

@@ -1,0 +1,55 @@
+"""The whole hot path captured into a CUDA graph through the asynchronous entry points gives
+the same bits as the synchronous calls, and a replay on fresh input gives them again."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2504_14338_gb300 import dopinf
+    return dopinf
+
+
+@pytest.mark.parametrize("gram_mode", ["ozaki", "fp64"])
+def test_graph_replay_matches_synchronous_calls(dp, gram_mode):
+    from paper_2504_14338_gb300 import synth
+    from paper_2504_14338_gb300.graph import PipelineGraph
+    w = synth.WORKLOADS["small"]
+    Qn, _ = synth.snapshots_numpy(w)
+    Q0 = torch.from_numpy(np.asarray(Qn)).cuda()
+    Q = dp.snapshot_matrix(w.n, w.k)
+    gm = dp.GRAM_OZAKI_FP64 if gram_mode == "ozaki" else dp.GRAM_FP64
+    r_list, r_cap, n_steps = [4, 6], 6, 400
+    b1 = synth.logspace(-8, 2, 4)
+    b2 = synth.logspace(-8, 2, 4)
+    mode, dt = dp.CONTINUOUS_RK4, w.snap_dt
+    # synchronous calls
+    Q.copy_(Q0)
+    dp.dopinf_transform(Q, w.var_row_offsets())
+    D = dp.dopinf_gram(Q, mode=gm)
+    red = dp.dopinf_reduce(D, r_cap=r_cap, r_fixed=r_cap)
+    ref = dp.dopinf_learn(red["Qhat"], r_list, b1, b2, n_steps, mode=mode, dt=dt)
+    # captured graph
+    Q.copy_(Q0)
+    pg = PipelineGraph(Q, w.var_row_offsets(), r_cap, r_list, b1, b2, n_steps, mode=mode, dt=dt, gram_mode=gm)
+    pg.capture()
+    for _ in range(2):  # each replay starts from the same input
+        Q.copy_(Q0)
+        pg.replay()
+        torch.cuda.synchronize()
+        assert pg.flags_value() == 0
+        assert torch.equal(pg.D, D)
+        assert torch.equal(pg.red["eigvals"], red["eigvals"])
+        assert torch.equal(pg.red["Qhat"], red["Qhat"])
+        assert int(pg.red["r"].item()) == red["r"]
+        for key in ("train_err", "growth", "status", "steps"):
+            assert torch.equal(pg.res[key], ref[key]), key
+        assert int(pg.res["best"].item()) == ref["best"]
+        assert torch.equal(pg.res["O_best"], ref["O_best"])
