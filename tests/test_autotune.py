@@ -1,0 +1,39 @@
+"""The autotuner's selection rule and bookkeeping on the host (timings injected)."""
+import pytest
+
+from paper_2504_14338_gb300 import autotune
+
+
+def test_pick_fastest_takes_the_minimum_and_the_first_on_ties():
+    assert autotune.pick_fastest({1: 5.0, 2: 3.0, 4: 4.0}) == 2
+    assert autotune.pick_fastest({4: 2.0, 8: 2.0, 1: 9.0}) == 4
+    assert autotune.pick_fastest({8: 1.0}) == 8
+
+
+def test_injected_timings_drive_the_choice(monkeypatch):
+    set_calls = []
+
+    class FakeDp:
+        DISCRETE = 0
+
+        @staticmethod
+        def dopinf_tune_learn_cluster(c):
+            set_calls.append(c)
+            return 4
+
+        @staticmethod
+        def dopinf_tune_reduce_coop(on):
+            set_calls.append(("coop", on))
+            return 1
+
+    monkeypatch.setattr(autotune, "dp", FakeDp)
+    monkeypatch.setattr(autotune, "_key", lambda *a: a)
+
+    class Q:
+        shape = (30, 600)
+
+    out = autotune.tune_learn(Q(), [10, 20, 30], [1] * 8, [1] * 8, 5000, timer={1: 9.0, 2: 6.0, 4: 4.5, 8: 5.0}.get)
+    assert out["best"] == 4 and out["rollout_ms"][4] == 4.5
+    assert set_calls[-1] == 4  # the winner is set process-wide
+    out = autotune.tune_reduce(Q(), 30, timer={1: 3.0, 0: 7.0}.get)
+    assert out["best"] == 1 and set_calls[-1] == ("coop", 1)

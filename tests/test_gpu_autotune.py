@@ -1,0 +1,61 @@
+"""The knobs the autotuner turns change where the work runs, not the results; the tuner picks
+one of them from measurements and leaves it set."""
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2504_14338_gb300 import dopinf as dp
+    from paper_2504_14338_gb300 import synth
+    from oracle import dopinf_oracle as O
+    w = synth.WORKLOADS["small"]
+    Qn, _ = synth.snapshots_numpy(w)
+    Q = O.transform(Qn, w.var_row_offsets())[0]
+    D = O.gram(Q)
+    Qh = O.reduce(D, r_fixed=16)["Qhat"]
+    return dp, synth, w, torch.from_numpy(D).cuda(), torch.from_numpy(Qh.T.copy()).cuda().t()
+
+
+def test_learn_same_bits_for_every_cluster_size(setup):
+    dp, synth, w, D, Qh = setup
+    b1 = synth.logspace(-8, 2, 4)
+    b2 = synth.logspace(-8, 2, 4)
+    prev = dp.dopinf_tune_learn_cluster(0)
+    runs = {}
+    try:
+        for c in (1, 2, 4, 8):
+            dp.dopinf_tune_learn_cluster(c)
+            runs[c] = dp.dopinf_learn(Qh, [6, 16], b1, b2, 400, mode=dp.CONTINUOUS_RK4, dt=w.snap_dt)
+    finally:
+        dp.dopinf_tune_learn_cluster(prev)
+    ref = runs[1]
+    assert (ref["status"] == 0).sum().item() >= 2
+    for c, res in runs.items():
+        assert res["best"] == ref["best"], c
+        for key in ("train_err", "growth", "status", "steps", "O_best"):
+            assert torch.equal(res[key], ref[key]), (c, key)
+
+
+def test_tuners_pick_a_measured_setting(setup):
+    dp, synth, w, D, Qh = setup
+    from paper_2504_14338_gb300 import autotune
+    b1 = synth.logspace(-8, 2, 4)
+    b2 = synth.logspace(-8, 2, 4)
+    prev_c, prev_r = dp.dopinf_tune_learn_cluster(0), dp.dopinf_tune_reduce_coop(-1)
+    try:
+        t = autotune.tune_learn(Qh, [6, 16], b1, b2, 400, mode=dp.CONTINUOUS_RK4, dt=w.snap_dt)
+        assert t["best"] in (1, 2, 4, 8) and len(t["rollout_ms"]) == 4
+        assert dp.dopinf_tune_learn_cluster(0) == t["best"]
+        assert min(t["rollout_ms"].values()) == t["rollout_ms"][t["best"]] > 0
+        r = autotune.tune_reduce(D, 16)
+        assert r["best"] in (0, 1) and dp.dopinf_tune_reduce_coop(-1) == r["best"]
+    finally:
+        dp.dopinf_tune_learn_cluster(prev_c)
+        dp.dopinf_tune_reduce_coop(prev_r)
