@@ -106,3 +106,60 @@ class PipelineGraph:
     def flags_value(self):
         """The OR of the DOPINF_FLAG_* bits raised so far (synchronises)."""
         return int(self.flags.item())
+
+
+class BatchedLearnGraph:
+    """Many independent learn problems (each its own reduced data Qhat, r list and grid) captured
+    into one CUDA graph: problem p runs on its own capture stream, forked from and joined back
+    to the capturing stream, so the graph's branches run concurrently.  Buffers per problem
+    are allocated up front; results stay on the device."""
+
+    def __init__(self, problems, n_steps, mode=dp.DISCRETE, dt=1.0, max_growth=1.2):
+        """problems: list of dict(Qhat=(r_max, k) column-major device tensor, r_list=[...],
+        beta1=[...], beta2=[...])."""
+        self.problems = problems
+        self.n_steps, self.mode, self.dt, self.max_growth = int(n_steps), int(mode), float(dt), float(max_growth)
+        self.out = []
+        self.bufs = []
+        for pr in problems:
+            Qh = pr["Qhat"]
+            r_max, k = Qh.shape
+            dev = Qh.device
+            n_cand = len(pr["r_list"]) * len(pr["beta1"]) * len(pr["beta2"])
+            d_max = max(r + r * (r + 1) // 2 + 1 for r in pr["r_list"])
+            self.out.append(dict(train_err=torch.empty(n_cand, dtype=torch.float64, device=dev),
+                                 growth=torch.empty(n_cand, dtype=torch.float64, device=dev),
+                                 status=torch.empty(n_cand, dtype=torch.int32, device=dev),
+                                 steps=torch.zeros(n_cand, dtype=torch.int64, device=dev),
+                                 best=torch.zeros(1, dtype=torch.int32, device=dev),
+                                 O_best=torch.zeros(d_max, r_max, dtype=torch.float64, device=dev).t(),
+                                 flags=torch.zeros(1, dtype=torch.int32, device=dev)))
+            rl = (ctypes.c_int * len(pr["r_list"]))(*[int(r) for r in pr["r_list"]])
+            nb = dp.lib.dopinf_learn_workspace(r_max, k, rl, len(pr["r_list"]), len(pr["beta1"]), len(pr["beta2"]))
+            w = dp.Workspace(dev)
+            self.bufs.append(w)
+            w.get(nb)
+        self.streams = [torch.cuda.Stream(device=problems[0]["Qhat"].device) for _ in problems]
+        self.graph = None
+
+    def _launch(self):
+        main = torch.cuda.current_stream()
+        for s in self.streams:
+            s.wait_stream(main)
+        for pr, out, w, s in zip(self.problems, self.out, self.bufs, self.streams):
+            with torch.cuda.stream(s):
+                dp.dopinf_learn_async(pr["Qhat"], pr["r_list"], pr["beta1"], pr["beta2"], self.n_steps, out,
+                                      mode=self.mode, dt=self.dt, max_growth=self.max_growth, ws=w, stream=s)
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def capture(self):
+        self._launch()  # eager warm-up
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._launch()
+        return self
+
+    def replay(self):
+        self.graph.replay()

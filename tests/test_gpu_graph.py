@@ -53,3 +53,29 @@ def test_graph_replay_matches_synchronous_calls(dp, gram_mode):
             assert torch.equal(pg.res[key], ref[key]), key
         assert int(pg.res["best"].item()) == ref["best"]
         assert torch.equal(pg.res["O_best"], ref["O_best"])
+
+
+def test_batched_learn_graph_matches_each_problem(dp):
+    """Several problems of uneven r (the batched-learn configuration at test scale: r drawn
+    from a range, a 6 x 6 grid each) in one captured graph, each equal to its own learn call."""
+    from paper_2504_14338_gb300 import synth
+    from paper_2504_14338_gb300.graph import BatchedLearnGraph
+    from oracle import dopinf_oracle as O
+    rng = np.random.default_rng(7)
+    problems = []
+    for p in range(4):
+        w = synth.Workload("batch%d" % p, 2, 512, int(rng.integers(160, 220)), int(rng.integers(6, 14)), seed=100 + p)
+        Qn, _ = synth.snapshots_numpy(w)
+        Q = O.transform(Qn, w.var_row_offsets())[0]
+        r = int(rng.integers(4, 9))
+        Qh = O.reduce(O.gram(Q), r_fixed=r)["Qhat"]
+        problems.append(dict(Qhat=torch.from_numpy(Qh.T.copy()).cuda().t(), r_list=[r - 2, r],
+                             beta1=synth.logspace(-8, 0, 6), beta2=synth.logspace(-4, 2, 6)))
+    bg = BatchedLearnGraph(problems, 300, mode=dp.DISCRETE).capture()
+    bg.replay()
+    torch.cuda.synchronize()
+    for pr, out in zip(problems, bg.out):
+        ref = dp.dopinf_learn(pr["Qhat"], pr["r_list"], pr["beta1"], pr["beta2"], 300)
+        assert int(out["best"].item()) == ref["best"]
+        for key in ("train_err", "growth", "status", "steps", "O_best"):
+            assert torch.equal(out[key], ref[key]), key
