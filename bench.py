@@ -219,6 +219,9 @@ def split_gram_measure(dp, synth, dev, frac=16):
     qs = reds["Qhat"].cpu().numpy()
     qerr = float(np.linalg.norm(qs - q64) / np.linalg.norm(q64))
     qerr20 = float(np.linalg.norm(qs[:20] - q64[:20]) / np.linalg.norm(q64[:20]))
+    # and at the r the retained-energy rule picks (tau = 0.9996) on the FP64 Gram
+    r_e = dp.dopinf_reduce(torch.from_numpy(D64).to(dev), r_cap=100, energy_target=0.9996)["r"]
+    qerr_e = float(np.linalg.norm(qs[:r_e] - q64[:r_e]) / np.linalg.norm(q64[:r_e]))
     useful = w.n * w.k * (w.k + 1)
     executed = 4 * 2 * w.n * w.k * (w.k + 128) / 2   # 4 products over the 128x128 upper tiles
     bf16 = 1978.2
@@ -232,6 +235,7 @@ def split_gram_measure(dp, synth, dev, frac=16):
             "fp64_ms_estimated": t64_sub * frac, "fp64_ms_on_1_of_%d_rows" % frac: t64_sub,
             "speedup_vs_fp64": t64_sub * frac / t_split,
             "top100_eig_err_rel_lambda1": eig_err, "qhat_err_r100": qerr, "qhat_err_r20": qerr20,
+            "energy_r": r_e, "qhat_err_energy_r": qerr_e,
             "errors_measured_on": "first n/%d rows" % frac, "transform_ms": t_transform,
             "transform_gbs": 3 * w.n * w.k * 4 / t_transform / 1e6}
 

@@ -108,9 +108,10 @@ int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
  *   chunks; the chunk partials are added in a fixed order.  Asynchronous.
  * DOPINF_GRAM_BF16X4: each value is split as x = h + l + e, h = bf16(x), l = bf16(x - h),
  *   and D ~= H^T H + H^T L + L^T H + L^T L on the tcgen05 tensor cores: FP32 accumulation
- *   over 64-row chunks, a compensated FP32 (TwoSum) running sum per work unit, FP64 sum of
- *   the units (|e| <= 2^-17 |x|).  Requires k <= 65535.  Synchronises the stream; returns
- *   DOPINF_E_TIMEOUT if an internal bounded wait expired (D is then not valid).
+ *   over 128-row chunks with H^T H in columns of its own, a compensated FP32 (TwoSum) running
+ *   sum per work unit, FP64 sum of the units (|e| <= 2^-17 |x|).  Requires k <= 65535.
+ *   Synchronises the stream; returns DOPINF_E_TIMEOUT if an internal bounded wait expired
+ *   (D is then not valid).
  * DOPINF_GRAM_OZAKI_FP64: column a is scaled by 2^-s_a (s_a bounding its max-abs) and cut
  *   into 8 integer digits of 7 bits (exact in BF16): x = 2^s_a sum_i d_i 2^(-7 i) + e,
  *   |e| <= 2^(s_a - 57).  The 36 digit products of weight 2..9 are summed on the tensor cores
@@ -124,8 +125,9 @@ int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
 size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode);
 /* Tuning of DOPINF_GRAM_BF16X4: rows summed by one FP32 tensor-memory accumulator before it
  * is added to the compensated (TwoSum) running sum (rounded up to a multiple of 64; default
- * 64).  The tensor core's FP32 accumulation rounds toward zero by about half an ulp per MMA,
- * so longer chunks trade accuracy (a relative bias growing with the chunk) for fewer drains.
+ * 128).  The tensor core's FP32 accumulation rounds toward zero by about half an ulp per MMA,
+ * so longer chunks trade accuracy (a relative bias growing linearly with the chunk: about
+ * -1.5e-9 per row of chunk on the diagonal) for fewer drains.
  * rows <= 0 only queries.  Returns the previous value.  Process-wide; not thread-safe against
  * concurrent dopinf_gram calls. */
 int64_t dopinf_tune_gram_chunk(int64_t rows);

@@ -9,24 +9,31 @@
 //
 // Accumulation.  The tensor core's FP32 accumulation rounds toward zero by about half an ulp
 // per MMA (measured on GB300: the diagonal of a long sum drifts low in proportion to the number
-// of MMAs).  So the MMA accumulator is restarted for every drain chunk (default: one stage of
-// 64 rows), the three small slice products of a stage are issued before the large H^T H one
-// (only 4 MMAs then add to a large accumulator), and each chunk sum is added to an FP32
-// (hi, lo) pair kept in tensor memory with Knuth's TwoSum, which carries the running sum to
-// about 2^-44; each drain thread keeps hi of its 64 columns in registers and lo in tensor
-// memory for the whole work unit (tile, row range), and at its end writes hi + lo in FP64.  A final kernel
-// adds the units of a tile in a fixed order and mirrors the upper triangle, so D is exactly
-// symmetric and reproducible run to run.
+// of MMAs).  So the MMA accumulator is restarted for every drain chunk (default: two stages of
+// 64 rows), the small slice products of a stage are issued before the large ones, and each
+// chunk sum is added to an FP32 (hi, lo) pair with Knuth's TwoSum, which carries the running
+// sum to about 2^-44.  A final kernel adds the units of a tile in a fixed order and mirrors the
+// upper triangle, so D is exactly symmetric and reproducible run to run.
 //
-// Kernel structure (one persistent CTA per SM, 320 threads):
+// The large product gets columns of its own.  The accumulator is 256 columns wide: one MMA with
+// the B operand [H_b; L_b] (the two slice tiles lie next to each other in shared memory) gives
+//     D_left = H_a^T H_b,  D_right = H_a^T L_b,
+// and two 128-column MMAs add L_a^T H_b and L_a^T L_b to D_right; the drain adds the halves.
+// Nothing small is ever added to the large H^T H sum, so the chunks can span two stages (the
+// per-chunk hand-off and drain cost as much as the MMAs at one stage) with the accuracy of
+// one-stage chunks, and 12 MMA instructions per stage instead of 16 (with 128-column MMAs only,
+// the issue loop, not the tensor pipe, set the pace).
+//
+// Kernel structure (one persistent CTA per SM, 576 threads):
 //   warp 0    TMA producer: H and L tiles of the a-block and of the b-block (128 snapshots x
 //             64 rows each, one contiguous 16 KB block of the tiled slice planes, 128-byte
 //             swizzle) into a 3-stage shared ring;
-//   warp 1    TMEM allocator and single-thread MMA issuer: tcgen05.mma M = 128, N = 128,
-//             K = 16 into one of two TMEM accumulators;
-//   warps 2-9 drain: tcgen05.ld of the finished accumulator, TwoSum into hi (registers) and
-//             lo (tensor memory).
-// TMEM columns: three 128-column accumulators (the MMA issuer runs two chunks ahead) and lo.
+//   warp 1    TMEM allocator and single-thread MMA issuer: tcgen05.mma M = 128, N = 256,
+//             K = 16 into one of two 256-column TMEM accumulators;
+//   warps 2-17 drain (four per TMEM lane quadrant, 32 columns each): tcgen05.ld of both halves
+//             of the finished accumulator, their sum added by
+//             TwoSum into (hi, lo) kept in registers for the whole work unit (tile, row range);
+//             at its end hi + lo is written in FP64.
 // Work units are ordered split-major, so the CTAs running together read the same rows and
 // the slices come from HBM about once.  Every mbarrier wait is bounded in time; on expiry the
 // kernel records an error, lets its copies and MMAs finish (again with bounded waits), frees
@@ -45,12 +52,12 @@ constexpr int STAGES = 3;
 constexpr uint32_t TILE = BM * BK * 2;         // 16 KB: one slice of one block
 constexpr uint32_t STAGE_BYTES = 4 * TILE;     // Ah, Al, Bh, Bl
 constexpr size_t SMEM_BYTES = STAGES * (size_t)STAGE_BYTES + 1024;
-constexpr int NDRAIN = 8;
+constexpr int NDRAIN = 16;
 constexpr int NTHREADS = 64 + 32 * NDRAIN;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int NACC = 3;  // TMEM accumulators of 128 columns; the fourth block holds lo
-constexpr uint32_t COL_LO = 384;
-int64_t g_chunk_rows = 64;  // rows summed by one MMA accumulator before the TwoSum drain (tunable)
+constexpr int NACC = 2;        // TMEM accumulators of 256 columns (left: H_b, right: L_b products)
+constexpr int ACC_COLS = 2 * BN;
+int64_t g_chunk_rows = 128;  // rows summed by one MMA accumulator before the TwoSum drain (tunable)
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kSmTarget = 152;  // the work split targets GB300's SM count, independent of the device queried
 
@@ -78,7 +85,8 @@ __device__ __forceinline__ float two_sum_hi(float hi, float a, float& err) {
   return s;
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+// 18 warps put 5 on two of the schedulers: 96 registers keep them inside one scheduler's file
+__global__ void __maxnreg__(96)
     gram_bf16x4_kernel(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapL, TcShape sh,
                        double* __restrict__ part, unsigned* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------------------- MMA issuer
-      const uint32_t idesc = idesc_bf16_f32(BM, BN);
+      const uint32_t idesc = idesc_bf16_f32(BM, ACC_COLS), idesc_half = idesc_bf16_f32(BM, BN);
       int stage = 0;
       int64_t it = 0, chunk = 0;
       bool issued = false;
@@ -163,7 +171,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t dacc = tmem + (uint32_t)(buf * BN);
+          const uint32_t dacc = tmem + (uint32_t)(buf * ACC_COLS);
           const int64_t c1 = c0 + sh.chunk_rows < k1 ? c0 + sh.chunk_rows : k1;
           bool first = true;
           for (int64_t row = c0; row < c1; row += BK) {
@@ -173,19 +181,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + (size_t)stage * STAGE_BYTES);
-            const uint32_t ah = sa, al = sa + TILE, bh = sa + 2 * TILE, bl = sa + 3 * TILE;
-            // the three small slice products first, then H^T H: only 4 MMAs add to a large sum
+            const uint32_t ah = sa, al = sa + TILE, bh = sa + 2 * TILE;  // L_b at bh + TILE
+            // H_a^T [H_b; L_b] -> [H^T H | H^T L] first (it starts the chunk's accumulator), then
+            // L_a^T H_b and L_a^T L_b into the right half only: the H^T H columns never receive a
+            // small addend, so their truncation is that of the H^T H products alone
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               const uint32_t o = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzled row
-              mma_bf16(dacc, sdesc_k_sw128(al + o), sdesc_k_sw128(bl + o), idesc, first && kk == 0 ? 0u : 1u);
-              mma_bf16(dacc, sdesc_k_sw128(ah + o), sdesc_k_sw128(bl + o), idesc, 1u);
-              mma_bf16(dacc, sdesc_k_sw128(al + o), sdesc_k_sw128(bh + o), idesc, 1u);
+              mma_bf16(dacc, sdesc_k_sw128(ah + o), sdesc_k_sw128(bh + o), idesc, first && kk == 0 ? 0u : 1u);
             }
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
               const uint32_t o = kk * 32;
-              mma_bf16(dacc, sdesc_k_sw128(ah + o), sdesc_k_sw128(bh + o), idesc, 1u);
+              mma_bf16(dacc + BN, sdesc_k_sw128(al + o), sdesc_k_sw128(bh + o), idesc_half, 1u);
+              mma_bf16(dacc + BN, sdesc_k_sw128(al + o), sdesc_k_sw128(bh + TILE + o), idesc_half, 1u);
             }
             issued = true;
             first = false;
@@ -204,18 +213,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {
-    // --------------------------------------------------------------- drain (warps 2-9)
+    // --------------------------------------------------------------- drain (warps 2-17)
     const int q = warp & 3;                  // TMEM lane quadrant this warp may access
-    const int c0w = ((warp - 2) >> 2) * 64;  // this warp's 64 columns
+    const int c0w = ((warp - 2) >> 2) * 32;  // this warp's 32 output columns
     const int row = q * 32 + lane;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int64_t chunk = 0;
     for (int u = blockIdx.x; u < sh.units && !abort_sh; u += gridDim.x) {
       const int64_t k0 = (int64_t)(u / sh.ntiles) * sh.rows_per_split;
       const int64_t k1 = k0 + sh.rows_per_split < sh.n ? k0 + sh.rows_per_split : sh.n;
-      float hi[64];
+      float hi[32], lo[32];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) hi[j] = 0.f;
+      for (int j = 0; j < 32; ++j) {
+        hi[j] = 0.f;
+        lo[j] = 0.f;
+      }
       bool ok = true;
       for (int64_t c0 = k0; c0 < k1; c0 += sh.chunk_rows) {
         const int buf = (int)(chunk % NACC);
@@ -226,43 +238,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        const bool first = c0 == k0;
-        // a 16-column quarter at a time: hi in registers, lo in tensor memory
+        const uint32_t acc = tmem + lane_off + (uint32_t)(buf * ACC_COLS) + (uint32_t)c0w;
+        // four columns at a time: left half (H_b products) + right half (L_b products)
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const uint32_t col = (uint32_t)(c0w + g * 16);
-          uint32_t a[16], lo[16];
-          tmem_ld_32x32b_x16(tmem + lane_off + (uint32_t)(buf * BN) + col, a);
-          if (!first) tmem_ld_32x32b_x16(tmem + lane_off + COL_LO + col, lo);
+        for (int g = 0; g < 8; ++g) {
+          uint32_t a[4], b[4];
+          tmem_ld_32x32b_x4(acc + (uint32_t)(g * 4), a);
+          tmem_ld_32x32b_x4(acc + (uint32_t)(BN + g * 4), b);
           tmem_wait_ld();
-          if (g == 3) {  // the accumulator is free once all quarters are loaded
+          if (g == 7) {  // the accumulator is free once every column is loaded
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar[buf]);
           }
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 4; ++j) {
             float e;
-            hi[g * 16 + j] = two_sum_hi(hi[g * 16 + j], __uint_as_float(a[j]), e);
-            lo[j] = first ? __float_as_uint(e) : __float_as_uint(__fadd_rn(__uint_as_float(lo[j]), e));
+            const float v = __fadd_rn(__uint_as_float(a[j]), __uint_as_float(b[j]));
+            hi[g * 4 + j] = two_sum_hi(hi[g * 4 + j], v, e);
+            lo[g * 4 + j] = __fadd_rn(lo[g * 4 + j], e);
           }
-          tmem_st_32x32b_x16(tmem + lane_off + COL_LO + col, lo);
         }
-        tmem_wait_st();
         ++chunk;
       }
       if (!ok) break;
       // unit finished: hi + lo of this warp's columns, in FP64, to the unit's partial tile
       double* P = part + (size_t)u * BM * BN;
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        uint32_t lo[32];
-        tmem_ld_32x32b_x32(tmem + lane_off + COL_LO + (uint32_t)(c0w + g * 32), lo);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          P[(size_t)(c0w + g * 32 + j) * BM + row] = (double)hi[g * 32 + j] + (double)__uint_as_float(lo[j]);
-      }
+      for (int j = 0; j < 32; ++j) P[(size_t)(c0w + j) * BM + row] = (double)hi[j] + (double)lo[j];
     }
   }
   tc_fence_before();

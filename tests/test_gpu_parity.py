@@ -122,9 +122,10 @@ def test_gram_row_partition_accumulates(dp):
 @pytest.mark.parametrize("n,k,dtype", [(100_003, 300, "f32"), (40_000, 257, "f64"), (5000, 64, "f32"), (70, 17, "f64")])
 def test_gram_bf16x4_vs_oracle(dp, n, k, dtype):
     # two BF16 slices per value leave |e| <= 2^-17 |x| out, with signs varying from row to
-    # row.  Each 64-row chunk is summed by 16 MMAs of which 4 add to a large accumulator, each
-    # rounding toward zero by at most one ulp: <= 4 * 2^-23 of the chunk's sum of |terms|,
-    # about 5e-7; the chunks are then summed with TwoSum (error ~2^-44).  Allowed: 2e-6.
+    # row.  The H^T H columns of a 128-row chunk receive the 8 MMAs of H^T H products only,
+    # each rounding toward zero by at most one ulp of the running chunk sum: <= 8 * 2^-23 of
+    # the chunk's sum of |terms|, about 1e-6 (the small products have columns of their own);
+    # the chunks are then summed with TwoSum (error ~2^-44).  Allowed: 2e-6.
     rng = np.random.default_rng(n + 7 * k)
     Qn = rng.standard_normal((n, k)) * np.exp(rng.uniform(-3, 3, k))
     if dtype == "f32":
