@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(256) digits_kernel(const T* __restrict__ Q, in
             d = ((V[u] + 64) & 127) - 64;
             V[u] = (V[u] - d) >> DIG_BITS;
           }
-          h[u] = __float2bfloat16_rn((float)d);
+          // |d| <= 128: through a 32-bit integer (a 64-bit integer conversion runs on the FP64 pipe)
+          h[u] = __float2bfloat16_rn((float)(int)d);
         }
         uint2 pk;
         pk.x = (unsigned)__bfloat16_as_ushort(h[0]) | ((unsigned)__bfloat16_as_ushort(h[1]) << 16);
