@@ -87,7 +87,7 @@ __device__ __forceinline__ void build_phi(const double* x, int r, int d, const u
   }
 }
 
-__global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
+__global__ void __launch_bounds__(RB, 5) rollout_kernel(RolloutBatch bt) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
@@ -137,21 +137,39 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
 
   const double dt = bt.dt, h2 = 0.5 * dt, h6 = dt / 6.0;
   const double denom = bt.metrics ? *cd.denom : 1.0;
-  double err = 0.0, gnum = 0.0;
+  // max over t < k of num/den (the training error is its square root: sqrt is monotone and
+  // correctly rounded, so this is the maximum of the square roots), and the bits of the
+  // largest |q - mu| (non-negative doubles order like their bit patterns)
+  double rat = 0.0;
+  unsigned long long gnumb = 0ull;
+  // growth >= max_growth, decided without a division outside a band of 2^-40 around the
+  // threshold (the division and the product each round by 2^-53)
+  const double thr = bt.max_growth * denom;
+  const bool band_ok = denom > 0.0 && isfinite(thr) && thr > 0.0;
+  const unsigned long long band_lo =
+      band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 - 0x1p-40)) : 0ull;
+  const unsigned long long band_hi =
+      band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + 0x1p-40)) : ~0ull;
   int st = 0;
   int64_t t_end = 0;  // the last state whose metrics were formed (= steps advanced)
   for (int64_t t = 0;; ++t) {
     t_end = t;
     // ---- metrics and output of state t (warp 0 of every CTA, identical results) ----
+    // They sit in front of the step's first evaluation, so they avoid the FP64 pipe where the
+    // result does not change: max |q - mu| as an integer maximum of the (non-negative) bit
+    // patterns, the training error as the maximum of num/den with one square root at the end,
+    // and the growth test against a band around max_growth * denom (the division only inside).
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       bool fin = true;
-      double dev = 0.0, num = 0.0, den = 0.0;
+      unsigned long long devb = 0ull;
+      double num = 0.0, den = 0.0;
       for (int i = lane; i < r; i += 32) {
         const double v = q[i];
         fin = fin && isfinite(v);
         if (bt.metrics) {
-          dev = fmax(dev, fabs(v - mu[i]));
+          const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v - mu[i]));
+          devb = b > devb ? b : devb;
           if (t < bt.k) {
             const double h = bt.Qhat[i + t * bt.ldqh];
             num += (v - h) * (v - h);
@@ -164,13 +182,16 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
       if (bt.metrics) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-          num += __shfl_xor_sync(0xffffffffu, num, o);
-          den += __shfl_xor_sync(0xffffffffu, den, o);
+          const unsigned long long ob = __shfl_xor_sync(0xffffffffu, devb, o);
+          devb = ob > devb ? ob : devb;
+          if (t < bt.k) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+          }
         }
         if (fin) {
-          gnum = fmax(gnum, dev);
-          if (t < bt.k) err = fmax(err, sqrt(num / den));
+          gnumb = devb > gnumb ? devb : gnumb;
+          if (t < bt.k) rat = fmax(rat, num / den);
         }
       }
       if (lane == 0) {
@@ -178,7 +199,8 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
         if (!fin) {
           st = 2;
           stop = 1;
-        } else if (bt.metrics && gnum / denom >= bt.max_growth) {
+        } else if (bt.metrics && gnumb >= band_lo &&
+                   (gnumb > band_hi || __longlong_as_double((long long)gnumb) / denom >= bt.max_growth)) {
           st = 3;
           stop = 1;
         }
@@ -235,8 +257,8 @@ __global__ void __launch_bounds__(RB) rollout_kernel(RolloutBatch bt) {
     if (bt.steps) bt.steps[cd.cand] = t_end;
     if (bt.metrics) {
       bt.status[cd.cand] = st;
-      bt.train_err[cd.cand] = st == 0 ? err : INFINITY;
-      bt.growth[cd.cand] = st == 2 ? INFINITY : gnum / denom;
+      bt.train_err[cd.cand] = st == 0 ? sqrt(rat) : INFINITY;
+      bt.growth[cd.cand] = st == 2 ? INFINITY : __longlong_as_double((long long)gnumb) / denom;
     }
     if (bt.traj && bt.finite) *bt.finite = st == 2 ? 0 : 1;
   }
