@@ -68,6 +68,17 @@ enum dopinf_rom_mode {
   DOPINF_CONTINUOUS_RK4 = 1  /* q' = A q + H (q x q)_u + c, central-difference derivatives, RK4 rollout */
 };
 
+/* Arithmetic of the rollouts of r <= 32 inside dopinf_learn / dopinf_learn_async (dopinf_rollout
+ * always uses FP64): binary64, or double-word binary32 pairs (about 48 significant bits, on the
+ * FP32 pipe) with compensated dot products.  Double-word candidates whose operator or initial
+ * state exceed 2^60 in magnitude, or whose state stops being finite, are rolled out again in
+ * FP64, so statuses and step counts follow the FP64 arithmetic; train_err and growth agree with
+ * it to rounding of order 1e-13 relative for stable rollouts. */
+enum dopinf_rollout_arith {
+  DOPINF_ROLLOUT_FP64 = 1,
+  DOPINF_ROLLOUT_DW = 2
+};
+
 /* Human-readable name of a status code (static storage). */
 const char* dopinf_status_string(int status);
 /* Text of the last CUDA error behind a DOPINF_E_CUDA in this host thread ("" if none);
@@ -236,10 +247,18 @@ int dopinf_tune_reduce_coop(int on);
  * n_b1, n_b2 <= 64 (DOPINF_E_UNSUPPORTED above).
  * Workspace: dopinf_learn_workspace(...) bytes.
  * ------------------------------------------------------------------------------------ */
-/* Tuning of dopinf_learn: preferred CTAs (1, 2, 4 or 8) of the thread-block cluster that rolls
- * out one candidate of r >= 16 (default 4); other values only query.  Returns the previous
- * value.  Process-wide. */
+/* Tuning of the row-split rollouts, used when some r of the list is above 32: preferred CTAs
+ * (1, 2, 4 or 8) of the thread-block cluster that rolls out one candidate of r >= 16 (default
+ * 4); other values only query.  Returns the previous value.  Process-wide. */
 int dopinf_tune_learn_cluster(int cluster);
+/* Tuning of the rollouts of r <= 32 (dopinf_learn, dopinf_learn_async, dopinf_rollout): rows
+ * of O per CTA, 1, 2 or 4 (default 2; raised where the cluster of ceil(r / rows) CTAs would
+ * exceed 16 or cannot be resident); other values only query.  Returns the previous value.
+ * Process-wide.  The results do not depend on it. */
+int dopinf_tune_rollout_rows(int rows);
+/* Rollout arithmetic of dopinf_learn for r <= 32: DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW
+ * (default); other values only query.  Returns the previous value.  Process-wide. */
+int dopinf_tune_rollout_arith(int arith);
 size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1,
                               int n_b2);
 int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list,

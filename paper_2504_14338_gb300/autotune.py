@@ -3,9 +3,10 @@
 Two knobs decide how the work is laid out on the GPU without changing a single bit of the
 results (both choices are exercised by the GPU tests):
 
-* the thread-block cluster that rolls out one candidate (1, 2, 4 or 8 CTAs splitting its
-  operator rows): small clusters duplicate less work while many candidates run, large ones
-  shorten each candidate's chain of dependent evaluations;
+* how many operator rows each CTA of a rollout cluster owns (1, 2 or 4, so ceil(r / rows) CTAs
+  per candidate; or, for r above 32, the cluster size 1, 2, 4 or 8 of the row-split kernel):
+  large clusters shorten each candidate's chain of evaluations, small ones leave more of the
+  GPU's FP64 issue to the other candidates;
 * the Householder tridiagonalisation as one cooperative launch (a grid barrier per column) or
   as three launches per column.
 
@@ -34,23 +35,28 @@ def _key(kind, *parts):
     return (kind, torch.cuda.get_device_name(), *parts)
 
 
-def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, clusters=(1, 2, 4, 8), reps=3,
-               ws=None, timer=None):
-    """Time the rollouts of this grid search for each cluster size; set and return the best.
+def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, clusters=(1, 2, 4, 8), rows=(1, 2, 4),
+               reps=3, ws=None, timer=None):
+    """Time the rollouts of this grid search for each launch shape; set and return the best.
 
-    timer(cluster) -> milliseconds replaces the measurement (host-logic tests)."""
+    Every r <= 32: operator rows per CTA of the column-owned rollouts (`rows`); otherwise the
+    cluster size of the row-split rollouts (`clusters`).  timer(setting) -> milliseconds
+    replaces the measurement (host-logic tests)."""
+    cols = max(int(r) for r in r_list) <= 32
+    setter = dp.dopinf_tune_rollout_rows if cols else dp.dopinf_tune_learn_cluster
+    settings = rows if cols else clusters
     key = _key("learn", tuple(r_list), len(beta1), len(beta2), int(n_steps), int(mode), int(Qhat.shape[1]))
     if timer is None and key in _cache:
-        dp.dopinf_tune_learn_cluster(_cache[key]["best"])
+        setter(_cache[key]["best"])
         return _cache[key]
-    prev = dp.dopinf_tune_learn_cluster(0)
+    prev = setter(0)
     times = {}
     try:
-        for c in clusters:
+        for c in settings:
             if timer is not None:
                 times[c] = float(timer(c))
                 continue
-            dp.dopinf_tune_learn_cluster(c)
+            setter(c)
             best_ms = None
             for _ in range(reps + 1):  # the first run warms up
                 res = dp.dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=mode, dt=dt, ws=ws)
@@ -58,10 +64,10 @@ def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, cl
                 best_ms = ms if best_ms is None else min(best_ms, ms)
             times[c] = best_ms
     finally:
-        dp.dopinf_tune_learn_cluster(prev)
+        setter(prev)
     best = pick_fastest(times)
-    dp.dopinf_tune_learn_cluster(best)
-    out = {"knob": "rollout cluster size", "best": best, "rollout_ms": times}
+    setter(best)
+    out = {"knob": "rollout rows per CTA" if cols else "rollout cluster size", "best": best, "rollout_ms": times}
     if timer is None:
         _cache[key] = out
     return out

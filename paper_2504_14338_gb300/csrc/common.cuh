@@ -110,6 +110,9 @@ size_t schur_cand_doubles(int r);
 int schur_solve(const SchurUnit* units_dev, const SchurUnit* units_host, int n_units, const SchurCand* cands_dev,
                 int n_cand, int* unit_fail, int* cand_status, cudaStream_t st);
 
+// Width of the quadratic OpInf data row [q, (q_i q_j)_{i<=j}, 1] for reduced dimension r.
+__host__ __device__ inline int dim_d(int r) { return r + r * (r + 1) / 2 + 1; }
+
 struct RolloutCand {
   const double* O;      // r x d column-major operator [A | H | c], leading dimension ldo
   int64_t ldo;
@@ -141,12 +144,27 @@ struct RolloutBatch {
   int traj;
   double* traj_out;
   int* finite;
+  // column-owned kernel (r <= 32): arithmetic (DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW), and
+  // redo = 1 for the FP64 pass over the candidates a double-word pass handed back (status 4)
+  int arith;
+  int redo;
 };
 
 size_t rollout_smem_bytes(int cluster, int r_max, int d_max);
 // Cluster size in {1, 2, 4, 8}, at least `want`, with the operator slice in shared memory; 0 if none fits.
 int rollout_cluster_size(int r_max, int d_max, int want);
 int launch_rollouts(RolloutBatch bt, int cluster, cudaStream_t st);
+// Column-owned rollouts (r <= 32): whether r is supported, the rows per CTA and cluster size a
+// launch for r would use (0 if none fits), the process-wide preferred rows per CTA (1, 2, 4;
+// other values only query; returns the previous value), and the launch of candidates
+// [cand0, cand0 + n) of one r (chained: programmatic dependent launch behind the previous
+// rollout launch on the stream, which it completes after).
+bool rollout_cols_supported(int r);
+int rollout_cols_shape(int r, int* rows, int* cluster);
+int rollout_set_rows(int rc);
+int rollout_set_arith(int a);
+int rollout_arith();
+int launch_rollouts_cols(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st);
 int learn_set_cluster(int c);
 
 }  // namespace dopinf

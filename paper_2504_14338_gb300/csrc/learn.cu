@@ -14,6 +14,8 @@
 // Then select_best takes the lowest training error among valid candidates (lowest index on
 // ties).  Everything is FP64.
 #include "common.cuh"
+
+#include <algorithm>
 #include <math.h>
 #include <vector>
 
@@ -88,8 +90,6 @@ __global__ void select_best(const double* err, const int* status, int n_cand, in
     if (status[c] == 0 && (b < 0 || err[c] < err[b])) b = c;
   *best = b;
 }
-
-__host__ __device__ inline int dim_d(int r) { return r + r * (r + 1) / 2 + 1; }
 
 constexpr int kMaxR = 64;  // entries of the r list
 
@@ -269,6 +269,17 @@ int learn_check(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const in
     if (!(beta2[i] >= 0.0)) return DOPINF_E_ARG;
   if (!ws || ws_bytes < dopinf_learn_workspace(r_max, k, r_list, n_r, n_b1, n_b2) || misaligned(ws))
     return DOPINF_E_ARG;
+  // rollouts: the column-owned kernel (one launch per r) when every r fits it, else the
+  // row-split kernel (cluster > 0) for all candidates in one launch
+  bool cols = true;
+  for (int i = 0; i < n_r && cols; ++i) {
+    int rc = 0, c = 0;
+    cols = rollout_cols_shape(r_list[i], &rc, &c) != 0;
+  }
+  if (cols) {
+    *cluster = -1;
+    return DOPINF_OK;
+  }
   *cluster = rollout_cluster_size(*r_used, *d_max, *r_used >= 16 ? g_cluster_want : 1);
   return *cluster ? DOPINF_OK : DOPINF_E_UNSUPPORTED;
 }
@@ -338,7 +349,30 @@ int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
   bt.growth = growth;
   bt.status = cand_status;
   bt.steps = cand_steps;
-  DOPINF_TRY(launch_rollouts(bt, cluster, st));
+  if (cluster > 0) {
+    DOPINF_TRY(launch_rollouts(bt, cluster, st));
+  } else {
+    // one launch per r, largest r (longest evaluations) first; each later launch is chained
+    // behind the one before by programmatic dependent launch, so all run side by side
+    int order[kMaxR];
+    for (int i = 0; i < n_r; ++i) order[i] = i;
+    std::sort(order, order + n_r, [&](int a, int b) { return r_list[a] > r_list[b] || (r_list[a] == r_list[b] && a < b); });
+    bt.arith = rollout_arith();
+    for (int j = 0; j < n_r; ++j) {
+      const int ir = order[j];
+      DOPINF_TRY(launch_rollouts_cols(bt, ir * n_pairs, n_pairs, r_list[ir], j > 0, st));
+    }
+    if (bt.arith == DOPINF_ROLLOUT_DW) {
+      // the FP64 pass over whatever the double-word pass handed back (usually nothing: its
+      // CTAs return at once); it starts once every double-word launch has completed
+      bt.arith = DOPINF_ROLLOUT_FP64;
+      bt.redo = 1;
+      for (int j = 0; j < n_r; ++j) {
+        const int ir = order[j];
+        DOPINF_TRY(launch_rollouts_cols(bt, ir * n_pairs, n_pairs, r_list[ir], j > 0, st));
+      }
+    }
+  }
   if (ev) DOPINF_CUDA(cudaEventRecord(ev[3], st));
   select_best<<<1, 32, 0, st>>>(train_err, cand_status, n_cand, w.best);
   gather_best<<<1, 256, 0, st>>>(w.best, w.cands, r_max, O_best, best_dev, dev_flags);
@@ -401,3 +435,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
 }
 
 DOPINF_API int dopinf_tune_learn_cluster(int cluster) { return learn_set_cluster(cluster); }
+
+DOPINF_API int dopinf_tune_rollout_rows(int rows) { return rollout_set_rows(rows); }
+
+DOPINF_API int dopinf_tune_rollout_arith(int arith) { return rollout_set_arith(arith); }

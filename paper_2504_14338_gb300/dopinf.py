@@ -23,6 +23,7 @@ F64, F32 = 0, 1
 CENTER, SCALE = 1, 2
 GRAM_FP64, GRAM_BF16X4, GRAM_OZAKI_FP64 = 0, 1, 2
 DISCRETE, CONTINUOUS_RK4 = 0, 1
+ROLLOUT_FP64, ROLLOUT_DW = 1, 2
 
 _c_i64 = ctypes.c_int64
 _c_p = ctypes.c_void_p
@@ -76,6 +77,8 @@ def _load():
                                         _c_sz, _c_p]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_tune_learn_cluster": (ctypes.c_int, [ctypes.c_int]),
+        "dopinf_tune_rollout_rows": (ctypes.c_int, [ctypes.c_int]),
+        "dopinf_tune_rollout_arith": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_reduce_coop": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_rollout": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_p, _c_i64, ctypes.c_int,
                                           ctypes.c_double, _c_p, _c_p, _c_p]),
@@ -210,8 +213,21 @@ def dopinf_tune_gram_chunk(rows=0):
 
 
 def dopinf_tune_learn_cluster(cluster=0):
-    """Sets (1, 2, 4, 8) or queries the rollout cluster size of dopinf_learn; returns the previous value."""
+    """Sets (1, 2, 4, 8) or queries the cluster size of the row-split rollouts (used when an r
+    of the list is above 32); returns the previous value."""
     return int(lib.dopinf_tune_learn_cluster(int(cluster)))
+
+
+def dopinf_tune_rollout_arith(arith=0):
+    """Sets (ROLLOUT_FP64, ROLLOUT_DW) or queries the arithmetic of the learn rollouts of r <= 32;
+    returns the previous value."""
+    return int(lib.dopinf_tune_rollout_arith(int(arith)))
+
+
+def dopinf_tune_rollout_rows(rows=0):
+    """Sets (1, 2, 4) or queries the operator rows per CTA of the rollouts of r <= 32 (the
+    cluster of one candidate has ceil(r / rows) CTAs, at most 16); returns the previous value."""
+    return int(lib.dopinf_tune_rollout_rows(int(rows)))
 
 
 def dopinf_tune_reduce_coop(on=-1):

@@ -22,6 +22,11 @@ def test_injected_timings_drive_the_choice(monkeypatch):
             return 4
 
         @staticmethod
+        def dopinf_tune_rollout_rows(c):
+            set_calls.append(("rows", c))
+            return 2
+
+        @staticmethod
         def dopinf_tune_reduce_coop(on):
             set_calls.append(("coop", on))
             return 1
@@ -32,8 +37,14 @@ def test_injected_timings_drive_the_choice(monkeypatch):
     class Q:
         shape = (30, 600)
 
-    out = autotune.tune_learn(Q(), [10, 20, 30], [1] * 8, [1] * 8, 5000, timer={1: 9.0, 2: 6.0, 4: 4.5, 8: 5.0}.get)
+    # r <= 32: rows per CTA of the column-owned rollouts
+    out = autotune.tune_learn(Q(), [10, 20, 30], [1] * 8, [1] * 8, 5000, timer={1: 9.0, 2: 4.0, 4: 6.5}.get)
+    assert out["best"] == 2 and out["rollout_ms"][2] == 4.0 and set(out["rollout_ms"]) == {1, 2, 4}
+    assert out["knob"] == "rollout rows per CTA"
+    assert set_calls[-1] == ("rows", 2)  # the winner is set process-wide
+    # an r above 32: cluster size of the row-split rollouts
+    out = autotune.tune_learn(Q(), [10, 40], [1] * 8, [1] * 8, 5000, timer={1: 9.0, 2: 6.0, 4: 4.5, 8: 5.0}.get)
     assert out["best"] == 4 and out["rollout_ms"][4] == 4.5
-    assert set_calls[-1] == 4  # the winner is set process-wide
+    assert set_calls[-1] == 4
     out = autotune.tune_reduce(Q(), 30, timer={1: 3.0, 0: 7.0}.get)
     assert out["best"] == 1 and set_calls[-1] == ("coop", 1)

@@ -274,8 +274,17 @@ def _reduced(r_fixed=6, seed=1234, **kw):
     return O.reduce(D, r_fixed=r_fixed)["Qhat"]
 
 
+@pytest.fixture(params=["dw", "fp64"])
+def arith(request, dp):
+    """The learn rollouts in double-word FP32 (the default) and in FP64."""
+    code = dp.ROLLOUT_DW if request.param == "dw" else dp.ROLLOUT_FP64
+    prev = dp.dopinf_tune_rollout_arith(code)
+    yield request.param
+    dp.dopinf_tune_rollout_arith(prev)
+
+
 @pytest.mark.parametrize("mode", ["discrete", "continuous"])
-def test_learn_vs_oracle(dp, mode):
+def test_learn_vs_oracle(dp, mode, arith):
     Qh = _reduced(r_fixed=6)
     k = Qh.shape[1]
     b1 = synth.logspace(-8, 2, 4)
@@ -311,6 +320,63 @@ def _learn_outputs(res):
     return [res["train_err"], res["growth"], res["status"], res["O_best"]]
 
 
+def test_learn_double_word_matches_fp64(dp):
+    """Double-word and FP64 rollouts of the same grid: the same statuses and step counts;
+    training errors and growths of the valid candidates within 1e-10 relative (rounding of the
+    two arithmetics).  An invalid candidate's growth is read at the step its rollout diverged,
+    where the divergence has amplified the rounding differences by an amount that depends on
+    the rollout: there both must be at or above the threshold."""
+    Qh = _reduced(r_fixed=12)
+    Qd = torch.from_numpy(Qh.T.copy()).cuda().t()
+    b1 = synth.logspace(-8, 2, 5)
+    b2 = synth.logspace(-8, 2, 5)
+    dt = synth.WORKLOADS["small"].snap_dt
+    prev = dp.dopinf_tune_rollout_arith(0)
+    try:
+        out = {}
+        for a in (dp.ROLLOUT_FP64, dp.ROLLOUT_DW):
+            dp.dopinf_tune_rollout_arith(a)
+            out[a] = dp.dopinf_learn(Qd, [4, 8, 12], b1, b2, 600, mode=dp.CONTINUOUS_RK4, dt=dt)
+    finally:
+        dp.dopinf_tune_rollout_arith(prev)
+    f, w = out[dp.ROLLOUT_FP64], out[dp.ROLLOUT_DW]
+    st = f["status"].cpu().numpy()
+    assert (st == 0).sum() >= 3
+    assert np.array_equal(st, w["status"].cpu().numpy())
+    assert np.array_equal(f["steps"].cpu().numpy(), w["steps"].cpu().numpy())
+    assert f["best"] == w["best"]
+    for key in ("train_err", "growth"):
+        a, b = f[key].cpu().numpy(), w[key].cpu().numpy()
+        fin = np.isfinite(a)
+        assert np.array_equal(fin, np.isfinite(b)), key
+        ok = fin & (st == 0)
+        rel = np.abs(a[ok] - b[ok]) / np.abs(a[ok])
+        assert rel.max() <= 1e-10, (key, rel.max())
+    gro = st == 3
+    assert np.all(f["growth"].cpu().numpy()[gro] >= 1.2) and np.all(w["growth"].cpu().numpy()[gro] >= 1.2)
+
+
+def test_learn_double_word_out_of_range_runs_fp64(dp):
+    """Reduced data far outside the double-word range (2^70 scale): every candidate is handed to
+    the FP64 kernel, so the results are bit for bit those of the FP64 arithmetic."""
+    Qh = _reduced(r_fixed=6) * 2.0 ** 70
+    Qd = torch.from_numpy(Qh.T.copy()).cuda().t()
+    b1 = synth.logspace(-8, 2, 3)
+    b2 = synth.logspace(-8, 2, 3)
+    prev = dp.dopinf_tune_rollout_arith(0)
+    try:
+        out = {}
+        for a in (dp.ROLLOUT_FP64, dp.ROLLOUT_DW):
+            dp.dopinf_tune_rollout_arith(a)
+            out[a] = dp.dopinf_learn(Qd, [4, 6], b1, b2, 300, mode=dp.CONTINUOUS_RK4,
+                                     dt=synth.WORKLOADS["small"].snap_dt)
+    finally:
+        dp.dopinf_tune_rollout_arith(prev)
+    assert out[dp.ROLLOUT_FP64]["best"] == out[dp.ROLLOUT_DW]["best"]
+    for key in ("train_err", "growth", "status", "steps", "O_best"):
+        assert torch.equal(out[dp.ROLLOUT_FP64][key], out[dp.ROLLOUT_DW][key]), key
+
+
 def test_learn_ignores_extra_qhat_rows(dp):
     """Qhat may hold more rows than the largest r of the list (every r uses its leading rows)."""
     Qh = _reduced(r_fixed=12)
@@ -339,3 +405,69 @@ def test_rollout_vs_oracle(dp):
         Qt = Qt.cpu().numpy()
         rel = np.linalg.norm(Qt - ref) / np.linalg.norm(ref)
         assert rel < 1e-8, (mode, rel)
+
+
+def _stable_operator(r, seed):
+    """A seeded quadratic operator [A | H | c] with a contracting linear part."""
+    rng = np.random.default_rng(seed)
+    d = r + r * (r + 1) // 2 + 1
+    Op = np.zeros((r, d))
+    Op[:, :r] = -0.5 * np.eye(r) + 0.05 * rng.standard_normal((r, r)) / np.sqrt(r)
+    Op[:, r:d - 1] = 0.02 * rng.standard_normal((r, d - r - 1)) / r
+    Op[:, d - 1] = 0.01 * rng.standard_normal(r)
+    return Op, 0.5 * rng.standard_normal(r)
+
+
+@pytest.mark.parametrize("r", [1, 2, 7, 16, 30, 32, 33, 36])
+def test_rollout_every_width_vs_oracle(dp, r):
+    """r <= 32 runs the column-owned kernel (1 to 5 column slots per thread), r > 32 the
+    row-split kernel; both against the oracle's rollout."""
+    Op, q0 = _stable_operator(r, 100 + r)
+    Od = torch.from_numpy(Op.T.copy()).cuda().t()
+    q0d = torch.from_numpy(q0.copy()).cuda()
+    for mode, mc, dt in [("discrete", 0, 1.0), ("continuous", 1, 1e-2)]:
+        ref = O.rollout(Op, r, q0, 300, mode=mode, dt=dt)
+        Qt, fin = dp.dopinf_rollout(Od, q0d, 300, mode=mc, dt=dt)
+        assert int(fin.item()) == 1
+        Qt = Qt.cpu().numpy()
+        assert np.array_equal(Qt[0], q0)
+        rel = np.linalg.norm(Qt - ref) / np.linalg.norm(ref)
+        assert rel < 1e-12, (r, mode, rel)
+
+
+@pytest.mark.parametrize("r", [5, 16, 30])
+def test_rollout_same_bits_for_every_rows_setting(dp, r):
+    """1, 2 or 4 operator rows per CTA (clusters of up to 16 CTAs) give the same trajectory."""
+    Op, q0 = _stable_operator(r, 7 * r)
+    Od = torch.from_numpy(Op.T.copy()).cuda().t()
+    q0d = torch.from_numpy(q0.copy()).cuda()
+    prev = dp.dopinf_tune_rollout_rows(0)
+    out = {}
+    try:
+        for rc in (1, 2, 4):
+            dp.dopinf_tune_rollout_rows(rc)
+            out[rc] = dp.dopinf_rollout(Od, q0d, 200, mode=1, dt=1e-2)[0]
+    finally:
+        dp.dopinf_tune_rollout_rows(prev)
+    for rc in (2, 4):
+        assert torch.equal(out[rc], out[1]), rc
+
+
+def test_rollout_nonfinite_stops_writing(dp):
+    """A rollout that overflows reports finite = 0 and leaves the rows after the first
+    non-finite state unwritten, like the oracle's trajectory up to that state."""
+    r = 6
+    Op, q0 = _stable_operator(r, 5)
+    Op[:, r:-1] *= 1e6  # a strongly quadratic map blows up within a few steps
+    q0 = q0 * 10
+    ref = O.rollout(Op, r, q0, 60, mode="discrete")
+    bad = int(np.argmax(~np.all(np.isfinite(ref), axis=1)))
+    assert bad > 0
+    Od = torch.from_numpy(Op.T.copy()).cuda().t()
+    Qt, fin = dp.dopinf_rollout(Od, torch.from_numpy(q0.copy()).cuda(), 60, mode=0)
+    assert int(fin.item()) == 0
+    Qt = Qt.cpu().numpy()
+    good = ref[:bad]
+    rel = np.abs(Qt[:bad] - good) / np.maximum(np.abs(good), 1e-300)
+    assert np.all(rel[np.isfinite(rel)] < 1e-8)
+    assert not np.all(np.isfinite(Qt[bad]))
