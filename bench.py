@@ -276,9 +276,9 @@ def gram_modes_measure(dp, Q, D_pipe, pipe_name, pipe_ms, ws):
 
 def sequential_learn_measure(dp, Qhat, w, mode):
     """The grid search one candidate at a time (one dopinf_learn call per (r, beta1, beta2),
-    one CTA per rollout): the unbatched baseline of the batched learn step."""
+    with the same kernels, arithmetic and launch shapes): the unbatched baseline of the
+    batched learn step."""
     import torch
-    prev = dp.dopinf_tune_learn_cluster(1)
     ws = dp.Workspace(Qhat.device)
     t0 = time.perf_counter()
     for r in w.r_list:
@@ -287,7 +287,6 @@ def sequential_learn_measure(dp, Qhat, w, mode):
                 dp.dopinf_learn(Qhat, [r], [b1], [b2], w.n_steps, mode=mode, dt=w.snap_dt, ws=ws)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    dp.dopinf_tune_learn_cluster(prev)
     return dt * 1e3
 
 
@@ -317,6 +316,12 @@ def main():
     dev = torch.device("cuda", local)
     QT = synth.snapshots_torch(w, dev)          # (k, n) row-major = column-major n x k
     Q = QT.t()
+    host_raw = None
+    if args.stage == "all" and not args.no_e2e:
+        # the raw snapshots in pinned host memory, for the end-to-end measurement (the device
+        # copy is transformed in place by every step)
+        host_raw = torch.empty(QT.shape, dtype=QT.dtype, pin_memory=True)
+        host_raw.copy_(QT)
     offs = w.var_row_offsets()
     b1, b2 = w.beta1s(), w.beta2s()
     r_max = max(w.r_list)
@@ -450,26 +455,44 @@ def main():
     gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
     modes = gram_modes_measure(dp, Q, last["D"], args.pipeline_gram, stage["gram"], ws) if rank == 0 else None
 
-    # e2e: host snapshot matrix (pinned) -> device, the pipeline through the C ABI, results back
+    # e2e: host snapshot matrices (pinned) -> device, the pipeline through the C ABI, results
+    # back to pinned host memory every step.  Pipelined (the public StreamingPipeline): the
+    # upload of step i + 1 runs on a copy stream while step i's captured pipeline computes.
+    # Serial, for reference: upload, then the eager pipeline, then the read-back.
     e2e = None
-    if not args.no_e2e:
-        host = torch.empty(QT.shape, dtype=QT.dtype, pin_memory=True)
-        host.copy_(QT)
-        n_e2e = max(1, min(args.steps, 2))
-        h2d = host.numel() * host.element_size()
+    if host_raw is not None:
+        from paper_2504_14338_gb300.graph import StreamingPipeline
+        sp = StreamingPipeline(host_raw, offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt,
+                               gram_mode=pipe_mode, device=dev)
+        sp.run([host_raw] * max(1, args.warmup))
+        torch.cuda.synchronize()
+        n_e2e = max(2, args.steps)
+        if world > 1:
+            dist.barrier()
+        s0 = time.perf_counter()
+        outs = sp.run([host_raw] * n_e2e)
+        e2e_s = (time.perf_counter() - s0) / n_e2e
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sp.h2d_bytes,
+               "d2h_bytes_per_step": sp.d2h_bytes, "ms_per_step": e2e_s * 1e3,
+               "how": "StreamingPipeline: two device copies of the snapshot matrix, the upload of step i+1 "
+                      "(pinned host -> device, copy stream) overlapping step i's captured pipeline; every "
+                      "step's results copied back to pinned host memory and read",
+               "best_index": outs[-1]["best"], "flags": outs[-1]["flags"]}
+        del sp, outs
+        torch.cuda.empty_cache()
+        # serial: copy, eager pipeline, read-back, one after the other
         torch.cuda.synchronize()
         s0 = time.perf_counter()
-        d2h = 0
         for _ in range(n_e2e):
-            QT.copy_(host, non_blocking=True)
+            QT.copy_(host_raw, non_blocking=True)
             res2 = step()
-            out = [res2["train_err"], res2["status"], res2["O_best"]]
-            outs = [o.cpu() for o in out]
-            d2h = sum(o.numel() * o.element_size() for o in outs)
+            outs = [o.cpu() for o in (res2["train_err"], res2["status"], res2["O_best"])]
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - s0) / n_e2e
-        e2e_val = world / e2e_s
-        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e["serial_value"] = world / ((time.perf_counter() - s0) / n_e2e)
 
     peaks = {}
     try:
@@ -490,21 +513,40 @@ def main():
         roll_flops += int(st_c) * evals * 2 * r_c * (r_c + r_c * (r_c + 1) // 2 + 1)
     roll_ms = float(np.mean([lp["rollouts"] for lp in ev["learn_parts"]]))
     roll_gf = roll_flops / (roll_ms / 1e3) / 1e9
-    roof = {"kernel": "rollout_kernel (batched ROM rollouts, one cluster of %d CTAs per candidate)"
-            % dp.dopinf_tune_learn_cluster(0), "bound": "alu",
-            "achieved": roll_gf, "peak": fp64_peak * 1e3, "unit": "GFLOP/s", "frac": roll_gf / (fp64_peak * 1e3),
-            "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)",
-            # dram__bytes_read + write of one ncu capture of this kernel on the same r, k, grid and
-            # horizon (the rollout's work does not depend on n): the operators, read once
-            "traffic": 10995200, "traffic_source": "profiles/rollout_kernel_stepflow_learn.md",
-            "algorithmic_flops_per_launch": roll_flops, "launch_ms": roll_ms,
-            "rhs_evaluations": int(steps_run.sum()) * evals}
+    rows = dp.dopinf_tune_rollout_rows(0)
+    arith = dp.dopinf_tune_rollout_arith(0)
+    if arith == dp.ROLLOUT_DW:
+        # double-word FP32 on the FP32 pipe: 152 SMs x 128 lanes x clock FP32 instructions per
+        # second, 13 of them per compensated multiply-add (12 per term + the phi product shared
+        # by the CTA's rows), 2 FP64-equivalent flops each
+        sm_mhz = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        dw_peak_gf = 152 * 128 * sm_mhz * 1e6 / 13.0 * 2 / 1e9
+        roof = {"kernel": "rollout_cols_kernel<double-word> (one launch per r, clusters of ceil(r/%d) CTAs)" % rows,
+                "bound": "alu", "achieved": roll_gf, "peak": dw_peak_gf, "unit": "GFLOP/s",
+                "frac": roll_gf / dw_peak_gf,
+                "peak_source": "double-word multiply-add rate = FP32 issue (152 SMs x 128 lanes x SM clock) / 13 "
+                               "FP32 instructions per compensated term, FP64-equivalent flops (derived)",
+                "fp64_equivalent_frac_of_fp64_peak": roll_gf / (fp64_peak * 1e3)}
+    else:
+        roof = {"kernel": "rollout_cols_kernel<fp64> (one launch per r, clusters of ceil(r/%d) CTAs)" % rows,
+                "bound": "alu", "achieved": roll_gf, "peak": fp64_peak * 1e3, "unit": "GFLOP/s",
+                "frac": roll_gf / (fp64_peak * 1e3),
+                "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)"}
+    roof.update({
+        # dram__bytes_read + write of one ncu capture of this kernel on the same r, k, grid and
+        # horizon (the rollout's work does not depend on n): the operators, read once; null
+        # until the capture of the current kernel is summarised under profiles/
+        "traffic": None, "traffic_source": None,
+        "algorithmic_flops_per_launch": roll_flops, "launch_ms": roll_ms,
+        "rhs_evaluations": int(steps_run.sum()) * evals,
+        "critical_path": "a valid candidate's %d steps x %d dependent evaluations, each closed by a cluster "
+                         "barrier" % (w.n_steps, evals)})
     # the Gram for context: the FP64-accurate Ozaki-digit product on the BF16 tensor cores
     tn = (w.k + 127) // 128
-    executed = 36 * 2 * 128 * 128 * ((w.n + 63) // 64 * 64) * (tn * (tn + 1) // 2)
+    executed = 28 * 2 * 128 * 128 * ((w.n + 63) // 64 * 64) * (tn * (tn + 1) // 2)  # 28 digit products
     if args.pipeline_gram == "ozaki":
         ach = executed / (stage["gram"] / 1e3) / 1e12
-        roof_gram = {"kernel": "ozaki_pass_kernel x 8 + colmax/digits/reduce (FP64-accurate Gram)", "bound": "tensor",
+        roof_gram = {"kernel": "ozaki_pass_kernel x 7 + colmax/digits/reduce (FP64-accurate Gram)", "bound": "tensor",
                      "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
                      "peak_source": "measured bf16 burst (of measured)", "algorithmic_flops_per_launch": executed,
                      "fp64_equivalent_tflops": gram_tf, "fp64_equivalent_vs_fp64_peak": gram_tf / fp64_peak}
@@ -515,11 +557,13 @@ def main():
     # kernels the library launches per step (transform, Gram, reduce with the cooperative
     # tridiagonalisation, learn: per r features + two TN products (2 each) + stats, the block-Schur
     # solve (build, 3 per forward panel, back substitution, candidates), rollouts, selection)
-    gram_launches = 11 if args.pipeline_gram == "ozaki" else 2
+    gram_launches = 10 if args.pipeline_gram == "ozaki" else 2
     s_max = max(w.r_list) * (max(w.r_list) + 1) // 2
     panels = (s_max + 31) // 32
     schur = 1 + 3 * panels + (2 * panels - 1) + 1
-    launches = 3 + gram_launches + 8 + (6 * len(w.r_list) + schur + 2)
+    # rollouts: one launch per r, and with double-word arithmetic one FP64 pass per r after it
+    roll_launches = len(w.r_list) * (2 if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else 1)
+    launches = 3 + gram_launches + 8 + (6 * len(w.r_list) + schur + 1 + roll_launches)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         per, desc, wall = oracle_sample(w)

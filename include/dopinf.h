@@ -123,15 +123,16 @@ int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
  *   sum per work unit, FP64 sum of the units (|e| <= 2^-17 |x|).  Requires k <= 65535.
  *   Synchronises the stream; returns DOPINF_E_TIMEOUT if an internal bounded wait expired
  *   (D is then not valid).
- * DOPINF_GRAM_OZAKI_FP64: column a is scaled by 2^-s_a (s_a bounding its max-abs) and cut
- *   into 8 integer digits of 7 bits (exact in BF16): x = 2^s_a sum_i d_i 2^(-7 i) + e,
- *   |e| <= 2^(s_a - 57).  The 36 digit products of weight 2..9 are summed on the tensor cores
+ * DOPINF_GRAM_OZAKI_FP64: column a is scaled by 2^-s_a (|x| < 2^(s_a - 1) on the column) and
+ *   cut into 7 balanced integer digits of 8 bits (|d| <= 128, exact in BF16):
+ *   x = 2^s_a sum_i d_i 2^(-8 i) + e, |e| <= 2^(s_a - 57).  The 28 digit products of weight
+ *   2..8 are summed on the tensor cores
  *   in row chunks whose partial sums are integers below 2^24 (exact), carried exactly by FP32
  *   TwoSum pairs and combined in FP64: an FP64-accurate D (the method of Ozaki et al. 2012).
  *   Requires k <= 65535.  Synchronises the stream; may return DOPINF_E_TIMEOUT.
  * Workspace: dopinf_gram_workspace(n, k, dtype, mode) bytes (BF16X4: 4 n k bytes of
- *   slices plus the per-unit FP64 partial tiles; OZAKI_FP64: 16 n k bytes of digits plus
- *   8 partial tiles per unit).
+ *   slices plus the per-unit FP64 partial tiles; OZAKI_FP64: 14 n k bytes of digits plus
+ *   7 partial tiles per unit).
  * ------------------------------------------------------------------------------------ */
 size_t dopinf_gram_workspace(int64_t n, int64_t k, int dtype, int mode);
 /* Tuning of DOPINF_GRAM_BF16X4: rows summed by one FP32 tensor-memory accumulator before it
@@ -252,7 +253,7 @@ int dopinf_tune_reduce_coop(int on);
  * 4); other values only query.  Returns the previous value.  Process-wide. */
 int dopinf_tune_learn_cluster(int cluster);
 /* Tuning of the rollouts of r <= 32 (dopinf_learn, dopinf_learn_async, dopinf_rollout): rows
- * of O per CTA, 1, 2 or 4 (default 2; raised where the cluster of ceil(r / rows) CTAs would
+ * of O per CTA, 1, 2 or 4 (default 4; raised where the cluster of ceil(r / rows) CTAs would
  * exceed 16 or cannot be resident); other values only query.  Returns the previous value.
  * Process-wide.  The results do not depend on it. */
 int dopinf_tune_rollout_rows(int rows);

@@ -3,19 +3,21 @@
 // Ogita, Oishi and Rump, "Error-free transformations of matrix multiplication", 2012).
 //
 // GB300 has about 1.1 TFLOP/s of FP64 but ~2 PFLOP/s of BF16 tensor throughput.  Each column a
-// of Q is scaled by 2^-s_a (s_a the exponent bounding its max-abs) and rounded to a 56-bit
-// fixed-point integer V, which is cut into S = 8 balanced base-128 digits (integer arithmetic
-// on the IEEE encoding; the FP64 pipe is not used):
-//     x = 2^s_a * sum_i d_i 2^(-7 i) + e,  |e| <= 2^(s_a - 57),
-// with |d_1| <= 128 and |d_i| <= 64 for i > 1, integers exact in BF16.  Then
-//     D_ab = 2^(s_a + s_b) * sum_w 2^(-7 w) S_w,   S_w = sum_{i + j = w} D_i^T D_j,
-// keeping the weights w = 2..9 (36 digit products; the dropped ones weigh <= 2^-70).
+// of Q is scaled by 2^-s_a (s_a = 1 + the exponent bounding its max-abs, so |x| < 2^(s_a - 1))
+// and rounded to a 55-bit fixed-point integer V = round(x 2^(56 - s_a)), which is cut into
+// S = 7 balanced base-256 digits (integer arithmetic on the IEEE encoding; the FP64 pipe is not
+// used):
+//     x = 2^s_a * sum_i d_i 2^(-8 i) + e,  |e| <= 2^(s_a - 57),
+// with |d_i| <= 128, integers exact in BF16.  Then
+//     D_ab = 2^(s_a + s_b) * sum_w 2^(-8 w) S_w,   S_w = sum_{i + j = w} D_i^T D_j,
+// keeping the weights w = 2..8 (28 digit products; the dropped ones weigh below 2^-55 of
+// 2^(s_a + s_b), as does the rounding of V).
 // Each S_w is formed in a pass of its own: a product of two digits is at most 2^14, so a
 // chunk of L rows of the m_w products of a weight is at most L m_w 2^14 < 2^24 when
 // L = 64 * floor(16 / m_w): every partial sum in the FP32 tensor accumulator is an integer
 // below 2^24 and therefore exact, whatever the accumulator's rounding.  Chunk sums go into an
 // FP32 (hi, lo) pair in tensor memory by TwoSum, exact while |lo| < 2^24 (at most 2^19 rows per
-// work unit); at the end of a unit hi + lo is weighted by 2^(-7 w) and stored in FP64 as the
+// work unit); at the end of a unit hi + lo is weighted by 2^(-8 w) and stored in FP64 as the
 // unit's partial tile of that weight (the drain threads keep hi of their 64 columns in
 // registers, lo in tensor memory).  A final kernel sums weights and units of a tile in a fixed order, applies
 // 2^(s_a + s_b) and mirrors the upper triangle.
@@ -34,8 +36,8 @@ namespace {
 using namespace sm100;
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int NDIG = 8;            // digits per value
-constexpr int DIG_BITS = 7;
+constexpr int NDIG = 7;            // digits per value
+constexpr int DIG_BITS = 8;
 constexpr int W_MIN = 2, W_MAX = NDIG + 1;
 constexpr int STAGES = 6;
 constexpr uint32_t TILE = BM * BK * 2;     // 16 KB
@@ -99,7 +101,7 @@ __device__ __forceinline__ void decode(float x, bool& neg, unsigned long long& m
   e2 = (ef ? ef : 1) - 150;
 }
 
-// max |Q[:, a]| per column, as the exponent s_a with max < 2^s_a (0 for an all-zero column).
+// max |Q[:, a]| per column, as s_a = 1 + the exponent e with max < 2^e (0 for an all-zero column).
 // Magnitudes compare as integers of their encodings.
 template <typename T>
 __global__ void __launch_bounds__(256) colmax_kernel(const T* __restrict__ Q, int64_t n, int64_t ldq, int* __restrict__ sexp) {
@@ -143,13 +145,13 @@ __global__ void __launch_bounds__(256) colmax_kernel(const T* __restrict__ Q, in
         decode(__longlong_as_double((long long)mx), neg, m, e2);
       else
         decode(__uint_as_float((unsigned)mx), neg, m, e2);
-      e = e2 + 64 - __clzll((long long)m);  // m 2^e2 < 2^e
+      e = e2 + 64 - __clzll((long long)m) + 1;  // m 2^e2 < 2^(e - 1)
     }
     sexp[a] = e;
   }
 }
 
-// V = round(x 2^(56 - s)) as a signed integer (|V| <= 2^56 for |x| < 2^s, error <= 1/2).
+// V = round(x 2^(56 - s)) as a signed integer (|V| <= 2^55 for |x| < 2^(s - 1), error <= 1/2).
 template <typename T>
 __device__ __forceinline__ long long fixed56(T x, int s) {
   bool neg;
@@ -159,7 +161,7 @@ __device__ __forceinline__ long long fixed56(T x, int s) {
   const int sh = e2 + 56 - s;  // V = m 2^sh
   unsigned long long u;
   if (sh >= 0)
-    u = m << sh;  // |x| < 2^s keeps this below 2^56
+    u = m << sh;  // |x| < 2^(s - 1) keeps this below 2^55
   else if (sh > -64)
     u = (m + (1ull << (-sh - 1))) >> (-sh);  // round half up in magnitude
   else
@@ -169,9 +171,9 @@ __device__ __forceinline__ long long fixed56(T x, int s) {
 
 // Digits into the tiled planes (plane p at p * nrb * ncb * 8192, block (cb, rb) inside it), by
 // integer arithmetic: V = round(x 2^(56 - s_a)) (error <= 2^(s_a - 57) in x), then balanced
-// base-128 digits from the low end, d_8 .. d_2 in [-64, 63], and the rest d_1 with |d_1| <= 128,
-// so that V = sum_i d_i 2^(7 (8 - i)).  A thread takes 4 consecutive rows of one column and
-// writes 8 bytes per plane; blockIdx.y walks the (padded) columns.
+// base-256 digits from the low end, d_7 .. d_2 in [-128, 127], and the rest d_1 with
+// |d_1| <= 128 (|V| <= 2^55), so that V = sum_i d_i 2^(8 (7 - i)).  A thread takes 4 consecutive
+// rows of one column and writes 8 bytes per plane; blockIdx.y walks the (padded) columns.
 constexpr int DIG_ROWS = 4;
 template <typename T>
 __global__ void __launch_bounds__(256) digits_kernel(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq,
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(256) digits_kernel(const T* __restrict__ Q, in
         for (int u = 0; u < DIG_ROWS; ++u) {
           long long d = V[u];
           if (p > 0) {
-            d = ((V[u] + 64) & 127) - 64;
+            d = ((V[u] + 128) & 255) - 128;
             V[u] = (V[u] - d) >> DIG_BITS;
           }
           // |d| <= 128: through a 32-bit integer (a 64-bit integer conversion runs on the FP64 pipe)

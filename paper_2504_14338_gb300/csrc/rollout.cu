@@ -718,7 +718,7 @@ void* cols_kernel(int nt, int rc, bool dw) {
   return tab[dw ? 1 : 0][nt - 1][ri]();
 }
 
-int g_rows_want = 2;  // tunable: rows of O per CTA in the column-owned rollouts
+int g_rows_want = 4;  // tunable: rows of O per CTA in the column-owned rollouts
 
 // Whether a cluster of c CTAs of this kernel can be resident (sizes above 8 need the
 // non-portable attribute and enough SMs in one GPC); cached per kernel and size.

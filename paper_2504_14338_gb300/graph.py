@@ -16,7 +16,9 @@ from . import dopinf as dp
 
 class PipelineGraph:
     def __init__(self, Q, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0,
-                 gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2):
+                 gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2, share=None):
+        """share: another PipelineGraph of the same sizes whose workspaces and output buffers
+        this one reuses (both graphs then run on one stream, one after the other)."""
         self.Q = Q
         n, k, ldq = dp._colmajor(Q)
         dev = Q.device
@@ -32,6 +34,14 @@ class PipelineGraph:
         self.beta2 = [float(b) for b in beta2]
         self.n_steps, self.mode, self.dt, self.max_growth = int(n_steps), int(mode), float(dt), float(max_growth)
         f64, i32 = torch.float64, torch.int32
+        self.graph = None
+        if share is not None:
+            if (share.n, share.k, share.r_cap, share.r_list, share.gram_mode) != (n, k, self.r_cap, self.r_list,
+                                                                                 gram_mode):
+                raise ValueError("share: the pipelines differ in size")
+            for name in ("flags", "mean", "scale", "D", "red", "res", "ws", "wbuf", "wsz"):
+                setattr(self, name, getattr(share, name))
+            return
         self.flags = torch.zeros(1, dtype=i32, device=dev)
         self.mean = torch.empty(n, dtype=f64, device=dev)
         self.scale = torch.empty(self.n_vars, dtype=f64, device=dev)
@@ -57,7 +67,6 @@ class PipelineGraph:
         self.ws = [dp.Workspace(dev) for _ in sizes]
         self.wbuf = [w.get(nb) for w, nb in zip(self.ws, sizes)]
         self.wsz = sizes
-        self.graph = None
 
     def _launch(self, stream):
         """The pipeline on `stream` through the asynchronous entry points (no host synchronisation)."""
@@ -106,6 +115,95 @@ class PipelineGraph:
     def flags_value(self):
         """The OR of the DOPINF_FLAG_* bits raised so far (synchronises)."""
         return int(self.flags.item())
+
+
+class StreamingPipeline:
+    """Steps II-IV over snapshot matrices that arrive one after another in pinned host memory.
+
+    Two device copies of the snapshot matrix, each with its own captured pipeline graph (the
+    workspaces and outputs are shared): while one graph runs, the next matrix is uploaded into
+    the other copy on a copy stream, so the host-to-device transfer hides behind the previous
+    step's compute.  Each step's results (training errors, statuses, the best index and its
+    operators, the failure flags) are copied back into pinned host memory on the compute
+    stream; result(i) waits for step i's copy and returns them.
+    """
+
+    OUTS = ("train_err", "status", "best", "O_best")
+
+    def __init__(self, host_QT, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE,
+                 dt=1.0, gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2,
+                 device="cuda"):
+        """host_QT: pinned CPU tensor (k, n), row-major, i.e. the column-major n x k snapshot matrix;
+        every submitted matrix has this shape and dtype.  The first one also serves for capture."""
+        if not host_QT.is_pinned():
+            raise ValueError("host_QT must be in pinned host memory")
+        dev = torch.device(device)
+        self.QT = [torch.empty(host_QT.shape, dtype=host_QT.dtype, device=dev) for _ in range(2)]
+        kw = dict(mode=mode, dt=dt, gram_mode=gram_mode, r_fixed=r_fixed, energy_target=energy_target,
+                  max_growth=max_growth)
+        self.pg = []
+        for b in range(2):
+            self.QT[b].copy_(host_QT)
+            share = self.pg[0] if b else None
+            self.pg.append(PipelineGraph(self.QT[b].t(), var_row_offsets, r_cap, r_list, beta1, beta2, n_steps,
+                                         share=share, **kw).capture())
+        torch.cuda.synchronize(dev)
+        self.stream = torch.cuda.Stream(device=dev)
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.free = [torch.cuda.Event() for _ in range(2)]      # graph b no longer reads QT[b]
+        self.uploaded = [torch.cuda.Event() for _ in range(2)]  # QT[b] holds the next matrix
+        self.fetched = [torch.cuda.Event() for _ in range(2)]   # host slot b holds a step's results
+        for e in self.free:
+            e.record(torch.cuda.current_stream(dev))
+        pg = self.pg[0]
+        srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
+        self.host_out = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in srcs] for _ in range(2)]
+        self.h2d_bytes = host_QT.numel() * host_QT.element_size()
+        self.d2h_bytes = sum(t.numel() * t.element_size() for t in srcs)
+        self.count = 0
+
+    def submit(self, host_QT):
+        """Queue one step on host_QT (pinned, the shape of the first); returns its index."""
+        i, b = self.count, self.count % 2
+        pg = self.pg[b]
+        # the upload into copy b waits for the graph that last read it (step i - 2)
+        self.copy_stream.wait_event(self.free[b])
+        with torch.cuda.stream(self.copy_stream):
+            self.QT[b].copy_(host_QT, non_blocking=True)
+            self.uploaded[b].record(self.copy_stream)
+        self.stream.wait_event(self.uploaded[b])
+        with torch.cuda.stream(self.stream):
+            pg.replay()
+            self.free[b].record(self.stream)
+            srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
+            for dst, src in zip(self.host_out[b], srcs):
+                dst.copy_(src, non_blocking=True)
+            pg.flags.zero_()
+            self.fetched[b].record(self.stream)
+        self.count += 1
+        return i
+
+    def result(self, i):
+        """Step i's results on the host (waits for them); valid until step i + 2 is submitted."""
+        if not (self.count - 2 <= i < self.count):
+            raise ValueError("result %d is no longer (or not yet) held" % i)
+        b = i % 2
+        self.fetched[b].synchronize()
+        out = dict(zip(self.OUTS, (t.clone() for t in self.host_out[b][:-1])))
+        out["best"] = int(out["best"][0])
+        out["flags"] = int(self.host_out[b][-1][0])
+        return out
+
+    def run(self, host_mats):
+        """Every matrix of host_mats through the pipeline; returns the list of results."""
+        out, first = [], self.count
+        for m in host_mats:
+            i = self.submit(m)
+            if i > first:
+                out.append(self.result(i - 1))
+        if self.count > first:
+            out.append(self.result(self.count - 1))
+        return out
 
 
 class BatchedLearnGraph:

@@ -79,3 +79,40 @@ def test_batched_learn_graph_matches_each_problem(dp):
         assert int(out["best"].item()) == ref["best"]
         for key in ("train_err", "growth", "status", "steps", "O_best"):
             assert torch.equal(out[key], ref[key]), key
+
+
+def test_streaming_pipeline_matches_synchronous_calls(dp):
+    """Matrices streamed from pinned host memory through the double-buffered pipeline (uploads
+    overlapping the previous step): each step's host results equal the synchronous calls on
+    that matrix, and a result slot is only reused two steps later."""
+    import dataclasses
+    from paper_2504_14338_gb300 import synth
+    from paper_2504_14338_gb300.graph import StreamingPipeline
+    base = synth.WORKLOADS["small"]
+    r_list, r_cap, n_steps = [4, 6], 6, 300
+    b1 = synth.logspace(-8, 2, 3)
+    b2 = synth.logspace(-8, 2, 3)
+    mode, dt = dp.CONTINUOUS_RK4, base.snap_dt
+    mats, refs = [], []
+    for seed in (11, 12, 13):
+        w = dataclasses.replace(base, seed=seed)
+        Qn, _ = synth.snapshots_numpy(w)
+        host = torch.empty((w.k, w.n), dtype=torch.float64, pin_memory=True)
+        host.copy_(torch.from_numpy(np.ascontiguousarray(np.asarray(Qn).T)))
+        mats.append(host)
+        Q = dp.snapshot_matrix(w.n, w.k)
+        Q.copy_(host.t())
+        dp.dopinf_transform(Q, w.var_row_offsets())
+        red = dp.dopinf_reduce(dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64), r_cap=r_cap, r_fixed=r_cap)
+        refs.append(dp.dopinf_learn(red["Qhat"], r_list, b1, b2, n_steps, mode=mode, dt=dt))
+    sp = StreamingPipeline(mats[0], base.var_row_offsets(), r_cap, r_list, b1, b2, n_steps, mode=mode, dt=dt)
+    outs = sp.run(mats + mats[::-1])
+    assert len(outs) == 6
+    for out, ref in zip(outs, refs + refs[::-1]):
+        assert out["flags"] == 0
+        assert out["best"] == ref["best"]
+        assert torch.equal(out["train_err"], ref["train_err"].cpu())
+        assert torch.equal(out["status"], ref["status"].cpu())
+        assert torch.equal(out["O_best"], ref["O_best"].cpu())
+    with pytest.raises(ValueError):
+        sp.result(0)

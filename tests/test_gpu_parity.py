@@ -159,8 +159,9 @@ def test_gram_bf16x4_eigenvalues_within_target(dp):
 
 @pytest.mark.parametrize("n,k,dtype", [(100_003, 300, "f64"), (4096, 200, "f64"), (20_011, 129, "f32"), (70, 17, "f64")])
 def test_gram_ozaki_fp64_vs_oracle(dp, n, k, dtype):
-    # exact digit products: the only errors are the 2^-57 digit truncation (relative to the
-    # column max) and the FP64 sums of the partials, far inside the FP64 path's bound
+    # exact digit products: the only errors are the digit truncation (2^-57 of the column's
+    # scale 2^s_a, plus dropped products below 2^-55 of it) and the FP64 sums of the partials,
+    # far inside the FP64 path's bound
     rng = np.random.default_rng(n + 3 * k)
     Qn = rng.standard_normal((n, k)) * np.exp(rng.uniform(-3, 3, k)) * np.exp(rng.uniform(-2, 2, (n, 1)))
     if dtype == "f32":
