@@ -316,10 +316,12 @@ def main():
     dev = torch.device("cuda", local)
     QT = synth.snapshots_torch(w, dev)          # (k, n) row-major = column-major n x k
     Q = QT.t()
-    host_raw = None
+    host_raw, host_cpus = None, None
     if args.stage == "all" and not args.no_e2e:
         # the raw snapshots in pinned host memory, for the end-to-end measurement (the device
-        # copy is transformed in place by every step)
+        # copy is transformed in place by every step), on the memory node next to the GPU
+        from paper_2504_14338_gb300.graph import bind_host_to_device
+        host_cpus = bind_host_to_device(dev)
         host_raw = torch.empty(QT.shape, dtype=QT.dtype, pin_memory=True)
         host_raw.copy_(QT)
     offs = w.var_row_offsets()
@@ -462,6 +464,16 @@ def main():
     e2e = None
     if host_raw is not None:
         from paper_2504_14338_gb300.graph import StreamingPipeline
+        # the upload alone (CUDA events), for reading the end-to-end number against
+        up = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            QT.copy_(host_raw, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            up.append(a.elapsed_time(b))
+        h2d_gbs = host_raw.numel() * host_raw.element_size() / (min(up) / 1e3) / 1e9
         sp = StreamingPipeline(host_raw, offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt,
                                gram_mode=pipe_mode, device=dev)
         sp.run([host_raw] * max(1, args.warmup))
@@ -481,7 +493,8 @@ def main():
                "how": "StreamingPipeline: two device copies of the snapshot matrix, the upload of step i+1 "
                       "(pinned host -> device, copy stream) overlapping step i's captured pipeline; every "
                       "step's results copied back to pinned host memory and read",
-               "best_index": outs[-1]["best"], "flags": outs[-1]["flags"]}
+               "best_index": outs[-1]["best"], "flags": outs[-1]["flags"],
+               "h2d_gbs_alone": h2d_gbs, "host_cpus": host_cpus}
         del sp, outs
         torch.cuda.empty_cache()
         # serial: copy, eager pipeline, read-back, one after the other

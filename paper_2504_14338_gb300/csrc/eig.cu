@@ -309,37 +309,104 @@ __device__ void tri_bounds(const double* d, const double* e, int64_t k, double& 
   hi += 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
 }
 
-// Number of eigenvalues of T smaller than x (Sturm sequence of the LDL^T pivots).
-__device__ int64_t sturm_count(const double* d, const double* e, int64_t k, double x, double pivmin) {
-  int64_t cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += q < 0.0;
+// Number of eigenvalues of T below x, without a division: the signs of the leading principal
+// minors p_i = det(T_i - x I), p_0 = 1, p_1 = d_0 - x, p_i = (d_{i-1} - x) p_{i-1} - e_{i-2}^2 p_{i-2},
+// change sign exactly as often (Sturm).  The quotient form q_i = p_i / p_{i-1} puts an FP64
+// division on the chain of every step; here the chain is one FMA.  The pair (p_{i-1}, p_i) is
+// rescaled by one exact power of two (exponent-field arithmetic) whenever p_i leaves
+// [2^-300, 2^300], and a p_i that vanishes against p_{i-1} (ratio below 2^-1000, or zero) is
+// replaced by -2^-1000 p_{i-1} (after bringing p_{i-1} near 1), the zero-pivot rule of the
+// quotient form.  e2[i] = e_i^2; T is scaled beforehand so that its norm is near 1
+// (tri_prep), which keeps every product of the recurrence far from overflow.
+__device__ __forceinline__ int exp_field(double v) {
+  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
+}
+__device__ __forceinline__ double pow2(int s) { return __longlong_as_double((long long)(1023 + s) << 52); }
+
+__device__ int64_t sturm_count_poly(const double* d, const double* e2, int64_t k, double x) {
+  double pm2 = 1.0, pm1 = d[0] - x;
+  if (exp_field(pm1) < 1023 - 1000) pm1 = -pow2(-1000);  // p_1 vanishes against p_0 = 1
+  int64_t cnt = pm1 < 0.0;
+#pragma unroll 4
   for (int64_t i = 1; i < k; ++i) {
-    q = d[i] - x - (e[i - 1] * e[i - 1]) / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    double p = fma(d[i] - x, pm1, -(e2[i - 1] * pm2));
+    const int ep = exp_field(p);
+    if (ep < 1023 - 300 || ep > 1023 + 300) {
+      const int em = exp_field(pm1);
+      if (ep == 0 || ep < em - 1000) {
+        // vanishing minor (counts as a sign change): p_{i-1} to [1, 2), p_i = -2^-1000 p_{i-1}
+        pm1 *= pow2(1023 - em);
+        p = -pm1 * pow2(-1000);
+      } else {
+        int sh = 1023 - ep;  // p to [1, 2) and p_{i-1} by the same factor
+        sh = sh > 1023 ? 1023 : (sh < -1022 ? -1022 : sh);
+        const double f = pow2(sh);
+        p *= f;
+        pm1 *= f;
+      }
+    }
+    cnt += (__double_as_longlong(p) ^ __double_as_longlong(pm1)) < 0;  // signs differ
+    pm2 = pm1;
+    pm1 = p;
   }
   return cnt;
 }
 
-// One warp per wanted eigenvalue (index idx in descending order = ascending index k-1-idx).
-// Each round evaluates 32 interior points of [lo, hi] and keeps the sub-interval that holds
-// the eigenvalue: a 33-fold reduction per round.
-__global__ void tri_multisect(const double* d, const double* e, int64_t k, int r_cap, double* lam, double* tnorm) {
+// T scaled by an exact power of two 2^-E with max(|d_i|, |e_i|) in [1, 2) (nothing to scale for
+// T = 0): ds, es and e2s = es^2, and the factor 2^E in *sc.  Counts and bisection run on the
+// scaled matrix; its eigenvalues times 2^E are those of T exactly.
+__global__ void __launch_bounds__(256) tri_prep(const double* d, const double* e, int64_t k, double* ds, double* es,
+                                                double* e2s, double* sc) {
+  __shared__ unsigned long long sh[256];
+  unsigned long long mb = 0;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(d[i]) & 0x7fffffffffffffffull;
+    const unsigned long long b =
+        i + 1 < k ? (unsigned long long)__double_as_longlong(e[i]) & 0x7fffffffffffffffull : 0ull;
+    mb = a > mb ? a : mb;
+    mb = b > mb ? b : mb;
+  }
+  sh[threadIdx.x] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long mx = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) mx = sh[i] > mx ? sh[i] : mx;
+    int ex = (int)(mx >> 52) - 1023;  // max in [2^ex, 2^(ex + 1)) (normal numbers)
+    if (mx == 0 || (mx >> 52) == 0 || (mx >> 52) == 0x7ff) ex = 0;
+    sh[0] = (unsigned long long)(long long)ex;
+  }
+  __syncthreads();
+  const int ex = (int)(long long)sh[0];
+  // 2^-ex in two factors so that neither leaves the normal range
+  const double f1 = pow2(-ex / 2), f2 = pow2(-ex - (-ex / 2));
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
+    ds[i] = d[i] * f1 * f2;
+    const double v = i + 1 < k ? e[i] * f1 * f2 : 0.0;
+    es[i] = v;
+    e2s[i] = v * v;
+  }
+  if (threadIdx.x == 0) *sc = pow2(ex / 2) * pow2(ex - ex / 2);
+}
+
+// One warp per wanted eigenvalue (index idx in descending order = ascending index k-1-idx) of the
+// scaled matrix (tri_prep).  Each round evaluates 32 interior points of [lo, hi] and keeps the
+// sub-interval that holds the eigenvalue: a 33-fold reduction per round.
+__global__ void tri_multisect(const double* d, const double* e, const double* e2, const double* sc, int64_t k,
+                              int r_cap, double* lam, double* tnorm) {
   const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (idx >= r_cap) return;
   double lo, hi, pivmin;
   tri_bounds(d, e, k, lo, hi, pivmin);
   const double tn = fmax(fabs(lo), fabs(hi));
-  if (idx == 0 && lane == 0) *tnorm = tn;
+  const double f = *sc;
+  if (idx == 0 && lane == 0) *tnorm = tn * f;
   const int64_t a = k - 1 - idx;  // ascending index
   for (int round = 0; round < 64; ++round) {
     const double width = hi - lo;
     if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_EPSILON * tn + 4.0 * pivmin) break;
     const double x = lo + width * (double)(lane + 1) / 33.0;
-    const int64_t c = sturm_count(d, e, k, x, pivmin);
+    const int64_t c = sturm_count_poly(d, e2, k, x);
     // the eigenvalue lies below x iff count(x) > a
     const unsigned above = __ballot_sync(0xffffffffu, c > a);
     const int first = above ? __ffs(above) - 1 : 32;  // first trial point above the eigenvalue
@@ -349,7 +416,7 @@ __global__ void tri_multisect(const double* d, const double* e, int64_t k, int r
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) lam[idx] = 0.5 * (lo + hi);
+  if (lane == 0) lam[idx] = 0.5 * (lo + hi) * f;
 }
 
 __device__ __forceinline__ double start_value(int64_t i, int j) {
@@ -361,84 +428,109 @@ __device__ __forceinline__ double start_value(int64_t i, int j) {
   return ((double)(h >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
 }
 
-// Inverse iteration, one thread per eigenvector; per-thread scratch is interleaved
-// (element i of vector j at [i * r_cap + j]) so that the threads' accesses coalesce.
-__global__ void tri_invit(const double* d, const double* e, int64_t k, int r_cap, const double* lam,
-                          const double* tnorm, double* Dg, double* Du, double* Du2, double* Dl,
-                          unsigned char* piv, double* Z) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// Inverse iteration, one warp per eigenvector, its working arrays in shared memory (k <= 4000;
+// above, in the per-vector slice of `scratch`, 6 k doubles each): lane 0 factors
+// T - lambda I = P L U (partial pivoting by rows) and runs the triangular sweeps, the warp forms
+// the start vector, the reciprocals of U's diagonal (so that the backward sweep multiplies
+// instead of dividing) and the norms.  Three iterations, then Z (element i of vector j at
+// [i * r_cap + j]).
+constexpr int64_t kInvitSmemK = 4000;
+__global__ void __launch_bounds__(32) tri_invit(const double* d, const double* e, int64_t k, int r_cap,
+                                                const double* lam, const double* tnorm, double* scratch, double* Z) {
+  extern __shared__ double smv[];
+  double* sm = k <= kInvitSmemK ? smv : scratch + (size_t)blockIdx.x * 6 * k;
+  double* Dg = sm;           // U diagonal, then its reciprocals
+  double* Du = sm + k;       // U first superdiagonal
+  double* Du2 = sm + 2 * k;  // U second superdiagonal (from row swaps)
+  double* Dl = sm + 3 * k;   // L multipliers
+  double* z = sm + 4 * k;
+  unsigned char* piv = reinterpret_cast<unsigned char*>(sm + 5 * k);
+  const int j = blockIdx.x, lane = threadIdx.x;
   if (j >= r_cap) return;
   const double lj = lam[j];
   const double eps_piv = DBL_EPSILON * fmax(*tnorm, DBL_MIN);
-#define AT(arr, i) arr[(size_t)(i) * r_cap + j]
-  for (int64_t i = 0; i < k; ++i) {
-    AT(Dg, i) = d[i] - lj;
-    if (i + 1 < k) {
-      AT(Du, i) = e[i];
-      AT(Dl, i) = e[i];
-    }
+  for (int64_t i = lane; i < k; i += 32) {
+    Dg[i] = d[i] - lj;
+    Du[i] = i + 1 < k ? e[i] : 0.0;
+    Dl[i] = i + 1 < k ? e[i] : 0.0;
+    Du2[i] = 0.0;
+    z[i] = start_value(i, j);
   }
-  // T - lambda I = P L U, partial pivoting by rows
-  for (int64_t i = 0; i + 1 < k; ++i) {
-    const double di = AT(Dg, i), li = AT(Dl, i);
-    if (fabs(di) >= fabs(li)) {
-      AT(piv, i) = 0;
-      const double f = di != 0.0 ? li / di : 0.0;
-      AT(Dl, i) = f;
-      AT(Dg, i + 1) = AT(Dg, i + 1) - f * AT(Du, i);
-      if (i + 2 < k) AT(Du2, i) = 0.0;
-    } else {
-      AT(piv, i) = 1;
-      const double f = di / li;
-      AT(Dg, i) = li;
-      AT(Dl, i) = f;
-      const double tmp = AT(Du, i);
-      const double dn = AT(Dg, i + 1);
-      AT(Du, i) = dn;
-      AT(Dg, i + 1) = tmp - f * dn;
-      if (i + 2 < k) {
-        const double un = AT(Du, i + 1);
-        AT(Du2, i) = un;
-        AT(Du, i + 1) = -f * un;
-      }
-    }
-  }
-  for (int64_t i = 0; i < k; ++i)
-    if (fabs(AT(Dg, i)) < eps_piv) AT(Dg, i) = AT(Dg, i) < 0.0 ? -eps_piv : eps_piv;
-  for (int64_t i = 0; i < k; ++i) AT(Z, i) = start_value(i, j);
-  for (int it = 0; it < 3; ++it) {
-    // forward: L^{-1} P b
+  __syncwarp();
+  if (lane == 0) {
     for (int64_t i = 0; i + 1 < k; ++i) {
-      const double f = AT(Dl, i);
-      if (AT(piv, i)) {
-        const double bi = AT(Z, i), bn = AT(Z, i + 1);
-        AT(Z, i) = bn;
-        AT(Z, i + 1) = bi - f * bn;
+      const double di = Dg[i], li = Dl[i];
+      if (fabs(di) >= fabs(li)) {
+        piv[i] = 0;
+        const double f = di != 0.0 ? li / di : 0.0;
+        Dl[i] = f;
+        Dg[i + 1] = Dg[i + 1] - f * Du[i];
       } else {
-        AT(Z, i + 1) = AT(Z, i + 1) - f * AT(Z, i);
+        piv[i] = 1;
+        const double f = di / li;
+        Dg[i] = li;
+        Dl[i] = f;
+        const double tmp = Du[i];
+        const double dn = Dg[i + 1];
+        Du[i] = dn;
+        Dg[i + 1] = tmp - f * dn;
+        if (i + 2 < k) {
+          const double un = Du[i + 1];
+          Du2[i] = un;
+          Du[i + 1] = -f * un;
+        }
       }
     }
-    // backward: U^{-1}
-    double nrm2 = 0.0;
-    for (int64_t i = k - 1; i >= 0; --i) {
-      double s = AT(Z, i);
-      if (i + 1 < k) s -= AT(Du, i) * AT(Z, i + 1);
-      if (i + 2 < k) s -= AT(Du2, i) * AT(Z, i + 2);
-      s /= AT(Dg, i);
-      AT(Z, i) = s;
-    }
-    double mx = 0.0;
-    for (int64_t i = 0; i < k; ++i) mx = fmax(mx, fabs(AT(Z, i)));
-    const double inv_mx = 1.0 / mx;
-    for (int64_t i = 0; i < k; ++i) {
-      const double z = AT(Z, i) * inv_mx;
-      nrm2 += z * z;
-      AT(Z, i) = z;
-    }
-    const double inv = 1.0 / sqrt(nrm2);
-    for (int64_t i = 0; i < k; ++i) AT(Z, i) *= inv;
   }
-#undef AT
+  __syncwarp();
+  for (int64_t i = lane; i < k; i += 32) {
+    double g = Dg[i];
+    if (fabs(g) < eps_piv) g = g < 0.0 ? -eps_piv : eps_piv;
+    Dg[i] = 1.0 / g;
+  }
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    if (lane == 0) {
+      // forward: L^{-1} P b
+      double zi = z[0];
+      for (int64_t i = 0; i + 1 < k; ++i) {
+        const double f = Dl[i], zn = z[i + 1];
+        if (piv[i]) {
+          z[i] = zn;
+          zi = zi - f * zn;
+        } else {
+          z[i] = zi;
+          zi = zn - f * zi;
+        }
+      }
+      z[k - 1] = zi;
+      // backward: U^{-1}, by the reciprocal pivots
+      double z1 = 0.0, z2 = 0.0;  // z[i + 1], z[i + 2]
+      for (int64_t i = k - 1; i >= 0; --i) {
+        const double s = (z[i] - Du[i] * z1 - Du2[i] * z2) * Dg[i];
+        z[i] = s;
+        z2 = z1;
+        z1 = s;
+      }
+    }
+    __syncwarp();
+    double mx = 0.0;
+    for (int64_t i = lane; i < k; i += 32) mx = fmax(mx, fabs(z[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double inv_mx = 1.0 / mx;
+    double nrm2 = 0.0;
+    for (int64_t i = lane; i < k; i += 32) {
+      const double v = z[i] * inv_mx;
+      nrm2 = fma(v, v, nrm2);
+      z[i] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+    const double inv = 1.0 / sqrt(nrm2);
+    __syncwarp();
+    for (int64_t i = lane; i < k; i += 32) z[i] *= inv;
+    __syncwarp();
+  }
+  for (int64_t i = lane; i < k; i += 32) Z[(size_t)i * r_cap + j] = z[i];
 }
 
 // Modified Gram-Schmidt (twice) of each vector against the earlier vectors of its cluster
@@ -538,8 +630,7 @@ __global__ void finalize_rank(const double* D, int64_t k, int64_t ldd, const dou
 }
 
 struct ReduceWs {
-  double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *Dg, *Du, *Du2, *Dl, *trace;
-  unsigned char* piv;
+  double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *iv, *trace, *ds, *es, *e2s, *sc;
   int* r;
   GridBar* bar;
   void* tn;
@@ -562,11 +653,11 @@ ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
   w.bar = c.take<GridBar>(1);
   w.Z = c.take<double>((size_t)k * r_cap);
   w.U = c.take<double>((size_t)k * r_cap);
-  w.Dg = c.take<double>((size_t)k * r_cap);
-  w.Du = c.take<double>((size_t)k * r_cap);
-  w.Du2 = c.take<double>((size_t)k * r_cap);
-  w.Dl = c.take<double>((size_t)k * r_cap);
-  w.piv = c.take<unsigned char>((size_t)k * r_cap);
+  w.iv = c.take<double>(k > kInvitSmemK ? (size_t)6 * k * r_cap : 1);  // inverse iteration, large k
+  w.ds = c.take<double>(k);  // the scaled tridiagonal of the bisection
+  w.es = c.take<double>(k);
+  w.e2s = c.take<double>(k);
+  w.sc = c.take<double>(1);
   w.tn_bytes = tn_workspace(k, r_cap, k, 0);
   w.tn = c.take<char>(w.tn_bytes);
   w.used = c.used;
@@ -648,8 +739,13 @@ int reduce_launch(const double* D, int64_t k, int64_t ldd, double energy_target,
   DOPINF_TRY(tridiagonalise(w, k, st));
   // one eigenvalue (a warp) and one eigenvector (a thread) per CTA: both are chains of FP64
   // divisions, so they are spread over the SMs rather than packed into a few warps
-  tri_multisect<<<r_cap, 32, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm);
-  tri_invit<<<r_cap, 1, 0, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.Dg, w.Du, w.Du2, w.Dl, w.piv, w.Z);
+  tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.ds, w.es, w.e2s, w.sc);
+  tri_multisect<<<r_cap, 32, 0, st>>>(w.ds, w.es, w.e2s, w.sc, k, r_cap, w.lam, w.tnorm);
+  DOPINF_TRY(launch_status());
+  const size_t iv_smem = k <= kInvitSmemK ? (size_t)k * (5 * sizeof(double) + 1) : 0;
+  if (iv_smem > 48 * 1024)
+    DOPINF_CUDA(cudaFuncSetAttribute(tri_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iv_smem));
+  tri_invit<<<r_cap, 32, iv_smem, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.iv, w.Z);
   tri_orth<<<1, EB, 0, st>>>(k, r_cap, w.lam, w.tnorm, w.Z);
   const size_t smem = (size_t)k * sizeof(double);
   if (smem > 48 * 1024) DOPINF_CUDA(cudaFuncSetAttribute(hh_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -117,6 +117,33 @@ class PipelineGraph:
         return int(self.flags.item())
 
 
+def bind_host_to_device(device):
+    """Restrict this process to the CPUs attached to `device` (sysfs local_cpulist of its PCI
+    function), so that host buffers allocated afterwards (first touch) sit on the memory node
+    nearest to it and its host-device copies take the shortest path.  Returns the CPU list, or
+    None where the topology is not published (nothing is changed then)."""
+    import os
+    try:
+        p = torch.cuda.get_device_properties(torch.device(device))
+        bus = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bus) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except (OSError, ValueError, AttributeError, RuntimeError):
+        return None
+
+
 class StreamingPipeline:
     """Steps II-IV over snapshot matrices that arrive one after another in pinned host memory.
 

@@ -231,6 +231,43 @@ def test_reduce_vs_oracle(dp, k, r_cap):
             assert err <= 1e3 * k * EPS * lam_ref[0] / gap + 1e-10, (j, err)
 
 
+@pytest.mark.parametrize("s", [-300, 300])
+def test_reduce_exact_under_power_of_two_scaling(dp, s):
+    """D and 2^s D (s even): every step scales exactly (norms, reflectors, the bisection on the
+    normalised tridiagonal, inverse iteration), so the eigenvalues scale by 2^s and T_r^T, Qhat by
+    2^(-s/2), 2^(s/2) bit for bit; far from 1 the Sturm recurrence rescales its minors."""
+    k, r_cap = 301, 10
+    rng = np.random.default_rng(77)
+    X = rng.standard_normal((2 * k, k)) @ np.diag(1.15 ** -np.arange(k))
+    D = X.T @ X
+    a = dp.dopinf_reduce(torch.from_numpy(D).cuda(), r_cap=r_cap, r_fixed=r_cap)
+    b = dp.dopinf_reduce(torch.from_numpy(np.ldexp(D, s)).cuda(), r_cap=r_cap, r_fixed=r_cap)
+    def host(t):
+        return t.cpu().numpy()
+    # np.ldexp scales exactly (a device pow(2, s) need not be exact)
+    assert np.array_equal(np.ldexp(host(a["eigvals"]), s), host(b["eigvals"]))
+    assert np.array_equal(np.ldexp(host(a["Tr"]), -s // 2), host(b["Tr"]))
+    assert np.array_equal(np.ldexp(host(a["Qhat"]), s // 2), host(b["Qhat"]))
+
+
+def test_reduce_large_k_vectors_outside_shared_memory(dp):
+    """k above the shared-memory size of inverse iteration (4000): eigenvalues against LAPACK's,
+    eigenvector residuals ||D u - lambda u|| against the FP64 bound."""
+    k, r_cap = 4001, 6
+    rng = np.random.default_rng(4001)
+    X = rng.standard_normal((k + 100, k)) @ np.diag(1.002 ** -np.arange(k))
+    D = X.T @ X
+    res = dp.dopinf_reduce(torch.from_numpy(D).cuda(), r_cap=r_cap, r_fixed=r_cap)
+    lam_ref = np.linalg.eigvalsh(D)[::-1][:r_cap]
+    lam = res["eigvals"].cpu().numpy()
+    assert np.all(np.abs(lam - lam_ref) <= 1e-10 * lam_ref + 8 * k * EPS * lam_ref[0])
+    U = res["Tr"].cpu().numpy() * np.sqrt(lam)
+    for j in range(r_cap):
+        u = U[:, j]
+        assert abs(np.linalg.norm(u) - 1.0) <= 1e-12
+        assert np.linalg.norm(D @ u - lam[j] * u) <= 1e3 * k * EPS * lam_ref[0]
+
+
 @pytest.mark.parametrize("k", [3, 4, 9, 200, 601])
 def test_reduce_cooperative_matches_per_column_launches(dp, k):
     """The one-launch tridiagonalisation (grid barrier per column) gives the same bits as
