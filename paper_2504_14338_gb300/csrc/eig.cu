@@ -199,15 +199,28 @@ __device__ void reflector_inplace(double* x, int64_t k, int64_t j, double* sh, d
   __syncthreads();
 }
 
+// Column c of the trailing matrix belongs to CTA c mod grid, warp (c div grid) mod 8, for the
+// whole reduction (every CTA gets its share, one column per scheduler while they last).  With
+// `resident`, a CTA keeps its columns in shared memory (slot c div grid) and reads them there;
+// every update is also written through to A, where the next step's column and the reflectors
+// are read by everyone.
 __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, double* d, double* e, double* tau,
-                                                      double* pg, GridBar* bar) {
+                                                      double* pg, GridBar* bar, int resident) {
   extern __shared__ double smd[];
   double* vj = smd;          // v_j (rows j+1..k-1)
   double* pj = smd + k;      // p_j
   double* vn = smd + 2 * k;  // column j+1 after update j, then v_{j+1}
+  double* own = smd + 3 * k; // resident: this CTA's columns
   __shared__ double sh[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * (TB / 32) + warp, nw = (int64_t)gridDim.x * (TB / 32);
+  const int64_t grid = gridDim.x;
+  if (resident) {
+    for (int64_t lc = 0; blockIdx.x + lc * grid < k; ++lc) {
+      const double* src = A + (blockIdx.x + lc * grid) * k;
+      for (int64_t r = threadIdx.x; r < k; r += blockDim.x) own[lc * k + r] = src[r];
+    }
+    __syncthreads();
+  }
   double tj = 0.0;  // tau of the pending update (0: none)
   for (int64_t j = -1; j + 2 < k; ++j) {
     // (a) the pending update of step j: alpha = -tau_j/2 (p_j . v_j), w = p + alpha v
@@ -264,18 +277,21 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
     // (d) update j on the trailing columns c >= j+2 (rows >= j+2), fused with p_{j+1}[c]
     if (tn != 0.0 || upd) {
       const int64_t r0 = c1 + 1;
-      // column c belongs to warp c mod nw for the whole reduction
-      for (int64_t c = r0 + ((gw - r0) % nw + nw) % nw; c < k; c += nw) {
+      for (int64_t lc = warp; blockIdx.x + lc * grid < k; lc += TB / 32) {
+        const int64_t c = blockIdx.x + lc * grid;
+        if (c < r0) continue;
         double* col = A + c * k;
+        double* cs = resident ? own + lc * k : col;
         const double vc = upd ? vj[c] : 0.0, wc = upd ? fma(alpha, vc, pj[c]) : 0.0;
         double s = 0.0;
         for (int64_t l = lane; l < k - r0; l += 32) {
           const int64_t r = r0 + l;
-          double a = __ldcg(col + r);
+          double a = resident ? cs[r] : __ldcg(col + r);
           if (upd) {
             const double wr = fma(alpha, vj[r], pj[r]);
             a = fma(-wr, vc, fma(-vj[r], wc, a));
             col[r] = a;
+            if (resident) cs[r] = a;
           }
           s = fma(a, vn[r], s);
         }
@@ -669,27 +685,32 @@ ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
 int g_reduce_coop = 1;
 
 int tridiagonalise(const ReduceWs& w, int64_t k, cudaStream_t st) {
-  const size_t smem = (size_t)3 * k * sizeof(double);
+  size_t smem = (size_t)3 * k * sizeof(double);
   DOPINF_CUDA(cudaMemsetAsync(w.bar, 0, sizeof(GridBar), st));
   int dev = 0, sms = 0, coop = 0;
   DOPINF_CUDA(cudaGetDevice(&dev));
   DOPINF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   DOPINF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (g_reduce_coop && k >= 3 && coop && smem <= 200 * 1024) {
+    // FP64 throughput per SM binds: about four trailing columns per CTA (one warp on each
+    // of the SM's four schedulers), at most one CTA per SM (a cheap barrier)
+    int64_t grid = (k - 1 + 3) / 4;
+    if (grid > sms) grid = sms;
+    if (grid < 1) grid = 1;
+    // the CTA's columns in shared memory where they fit
+    const int64_t ncl = (k + grid - 1) / grid;
+    const size_t smem_res = (size_t)(3 + ncl) * k * sizeof(double);
+    int resident = smem_res <= 200 * 1024 ? 1 : 0;
+    if (resident) smem = smem_res;
     DOPINF_CUDA(cudaFuncSetAttribute(hh_tridiag_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     DOPINF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hh_tridiag_coop, TB, smem));
     if (per_sm >= 1) {
-      // FP64 throughput per SM binds: about four trailing columns per CTA (one warp on each
-      // of the SM's four schedulers), at most one CTA per SM (a cheap barrier)
-      int64_t grid = (k - 1 + 3) / 4;
-      if (grid > sms) grid = sms;
-      if (grid < 1) grid = 1;
       double* A = w.A;
       double *d = w.d, *e = w.e, *tau = w.tau, *p = w.p;
       GridBar* bar = w.bar;
       int64_t kk = k;
-      void* args[] = {&A, &kk, &d, &e, &tau, &p, &bar};
+      void* args[] = {&A, &kk, &d, &e, &tau, &p, &bar, &resident};
       DOPINF_CUDA(cudaLaunchCooperativeKernel((const void*)hh_tridiag_coop, dim3((unsigned)grid), dim3(TB), args, smem, st));
       return launch_status();  // the barrier's error word is read with the results
     }
