@@ -546,10 +546,11 @@ def main():
                 "frac": roll_gf / (fp64_peak * 1e3),
                 "peak_source": "FP64 = measured bf16 burst x nominal 1.25/2250 (of measured)"}
     roof.update({
-        # dram__bytes_read + write of one ncu capture of this kernel on the same r, k, grid and
-        # horizon (the rollout's work does not depend on n): the operators, read once; null
-        # until the capture of the current kernel is summarised under profiles/
-        "traffic": None, "traffic_source": None,
+        # DRAM bytes of one ncu capture of the r = 30 launch on the same r, k, grid and horizon
+        # (the rollout's work does not depend on n): the operators, read once
+        "traffic": 8.3e6, "traffic_scope": "the r = 30 launch alone (the stage's largest; its operators, "
+                                            "7.6 MB, read once)",
+        "traffic_source": "profiles/rollout_cols_kernel_stepflow_learn.md",
         "algorithmic_flops_per_launch": roll_flops, "launch_ms": roll_ms,
         "rhs_evaluations": int(steps_run.sum()) * evals,
         "critical_path": "a valid candidate's %d steps x %d dependent evaluations, each closed by a cluster "
@@ -576,7 +577,10 @@ def main():
     schur = 1 + 3 * panels + (2 * panels - 1) + 1
     # rollouts: one launch per r, and with double-word arithmetic one FP64 pass per r after it
     roll_launches = len(w.r_list) * (2 if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else 1)
-    launches = 3 + gram_launches + 8 + (6 * len(w.r_list) + schur + 1 + roll_launches)
+    # transform 3; reduce 9 (tridiagonalisation, scaling, multisection, inverse iteration,
+    # orthogonalisation, back-transform, the Q-hat product (2), rank); learn: candidate tables,
+    # per r features + two TN products (2 each) + statistics, the solves, rollouts, selection (2)
+    launches = 3 + gram_launches + 9 + (1 + 6 * len(w.r_list) + schur + roll_launches + 2)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         per, desc, wall = oracle_sample(w)
