@@ -163,8 +163,10 @@ __global__ void finalize_scale(double* var_scale, int n_vars, int scale, unsigne
 // division; operands near the ends of the exponent range (zero, subnormal, huge, non-finite)
 // take the IEEE division, so the result equals c / s bit for bit everywhere.
 __device__ __forceinline__ double div_by(double c, double s, double y, bool s_ok) {
-  const double a = fabs(c);
-  if (!s_ok || !(a >= 0x1p-900 && a <= 0x1p+900)) return __ddiv_rn(c, s);
+  // |c| in [2^-900, 2^900), read from the exponent field: an integer test, where a
+  // floating-point compare would take GB300's FP64 pipe (an issue slot per compare)
+  const int ec = (int)(((unsigned long long)__double_as_longlong(c) >> 52) & 0x7ff);
+  if (!s_ok || ec < 1023 - 900 || ec >= 1023 + 900) return __ddiv_rn(c, s);
   const double q0 = __dmul_rn(c, y);
   const double rem = __fma_rn(-q0, s, c);
   return __fma_rn(rem, y, q0);

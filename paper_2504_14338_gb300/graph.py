@@ -68,16 +68,21 @@ class PipelineGraph:
         self.wbuf = [w.get(nb) for w, nb in zip(self.ws, sizes)]
         self.wsz = sizes
 
-    def _launch(self, stream):
-        """The pipeline on `stream` through the asynchronous entry points (no host synchronisation)."""
+    def _launch(self, stream, front=True, back=True):
+        """The pipeline on `stream` through the asynchronous entry points (no host synchronisation):
+        front = transform and Gram (the steps that read Q), back = reduce and learn."""
         L, P, s = dp.lib, dp._ptr, dp._stream(stream)
         red, res = self.red, self.res
-        dp._check("dopinf_transform", L.dopinf_transform(
-            P(self.Q), dp._dtype_code(self.Q), self.n, self.k, self.ldq, self.n_vars, self.offs,
-            dp.CENTER | dp.SCALE, P(self.mean), P(self.scale), P(self.flags), P(self.wbuf[0]), self.wsz[0], s))
-        dp._check("dopinf_gram_async", L.dopinf_gram_async(
-            P(self.Q), dp._dtype_code(self.Q), self.n, self.k, self.ldq, self.gram_mode, 0, P(self.D),
-            self.D.stride(0), P(self.flags), P(self.wbuf[1]), self.wsz[1], s))
+        if front:
+            dp._check("dopinf_transform", L.dopinf_transform(
+                P(self.Q), dp._dtype_code(self.Q), self.n, self.k, self.ldq, self.n_vars, self.offs,
+                dp.CENTER | dp.SCALE, P(self.mean), P(self.scale), P(self.flags), P(self.wbuf[0]), self.wsz[0],
+                s))
+            dp._check("dopinf_gram_async", L.dopinf_gram_async(
+                P(self.Q), dp._dtype_code(self.Q), self.n, self.k, self.ldq, self.gram_mode, 0, P(self.D),
+                self.D.stride(0), P(self.flags), P(self.wbuf[1]), self.wsz[1], s))
+        if not back:
+            return
         dp._check("dopinf_reduce_async", L.dopinf_reduce_async(
             P(self.D), self.k, self.D.stride(0), self.energy_target, self.r_fixed, self.r_cap, P(red["r"]),
             P(red["trace"]), P(red["eigvals"]), P(red["Tr"]), P(red["Qhat"]), P(self.flags), P(self.wbuf[2]),
@@ -96,21 +101,40 @@ class PipelineGraph:
         """One pass without the graph (the same launches, issued from the host)."""
         self._launch(stream if stream is not None else torch.cuda.current_stream())
 
-    def capture(self):
-        """Capture the pipeline into a CUDA graph (after one eager warm-up pass)."""
+    def capture(self, split=False):
+        """Capture the pipeline into a CUDA graph (after one eager warm-up pass).  split: two
+        graphs instead, graph_front (transform, Gram) and graph_back (reduce, learn), replayed by
+        replay_front / replay_back, so that a caller may place work between them."""
         side = torch.cuda.Stream(device=self.Q.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             self._launch(side)
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
+        if split:
+            self.graph_front, self.graph_back = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph_front):
+                self._launch(torch.cuda.current_stream(), back=False)
+            with torch.cuda.graph(self.graph_back):
+                self._launch(torch.cuda.current_stream(), front=False)
+            return self
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
             self._launch(torch.cuda.current_stream())
         return self
 
     def replay(self):
-        self.graph.replay()
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.graph_front.replay()
+            self.graph_back.replay()
+
+    def replay_front(self):
+        self.graph_front.replay()
+
+    def replay_back(self):
+        self.graph_back.replay()
 
     def flags_value(self):
         """The OR of the DOPINF_FLAG_* bits raised so far (synchronises)."""
@@ -147,10 +171,12 @@ def bind_host_to_device(device):
 class StreamingPipeline:
     """Steps II-IV over snapshot matrices that arrive one after another in pinned host memory.
 
-    Two device copies of the snapshot matrix, each with its own captured pipeline graph (the
-    workspaces and outputs are shared): while one graph runs, the next matrix is uploaded into
-    the other copy on a copy stream, so the host-to-device transfer hides behind the previous
-    step's compute.  Each step's results (training errors, statuses, the best index and its
+    Two device copies of the snapshot matrix, each with its own captured front graph
+    (transform and Gram, the steps that read the matrix); reduce and learn form one shared back
+    graph (the workspaces and outputs are shared).  The next matrix is uploaded into the other
+    copy on a copy stream once the current step's Gram has finished, so the transfer hides behind
+    the reduce and learn steps and its writes do not pass through L2 while the Gram's digit
+    planes live there.  Each step's results (training errors, statuses, the best index and its
     operators, the failure flags) are copied back into pinned host memory on the compute
     stream; result(i) waits for step i's copy and returns them.
     """
@@ -173,15 +199,14 @@ class StreamingPipeline:
             self.QT[b].copy_(host_QT)
             share = self.pg[0] if b else None
             self.pg.append(PipelineGraph(self.QT[b].t(), var_row_offsets, r_cap, r_list, beta1, beta2, n_steps,
-                                         share=share, **kw).capture())
+                                         share=share, **kw).capture(split=True))
         torch.cuda.synchronize(dev)
         self.stream = torch.cuda.Stream(device=dev)
         self.copy_stream = torch.cuda.Stream(device=dev)
-        self.free = [torch.cuda.Event() for _ in range(2)]      # graph b no longer reads QT[b]
+        self.gram_done = torch.cuda.Event()                      # the last queued front graph finished
         self.uploaded = [torch.cuda.Event() for _ in range(2)]  # QT[b] holds the next matrix
         self.fetched = [torch.cuda.Event() for _ in range(2)]   # host slot b holds a step's results
-        for e in self.free:
-            e.record(torch.cuda.current_stream(dev))
+        self.gram_done.record(torch.cuda.current_stream(dev))
         pg = self.pg[0]
         srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
         self.host_out = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in srcs] for _ in range(2)]
@@ -193,15 +218,17 @@ class StreamingPipeline:
         """Queue one step on host_QT (pinned, the shape of the first); returns its index."""
         i, b = self.count, self.count % 2
         pg = self.pg[b]
-        # the upload into copy b waits for the graph that last read it (step i - 2)
-        self.copy_stream.wait_event(self.free[b])
+        # the upload into copy b waits for the last queued Gram (step i - 1's, which also
+        # follows step i - 2's, the last reader of copy b)
+        self.copy_stream.wait_event(self.gram_done)
         with torch.cuda.stream(self.copy_stream):
             self.QT[b].copy_(host_QT, non_blocking=True)
             self.uploaded[b].record(self.copy_stream)
         self.stream.wait_event(self.uploaded[b])
         with torch.cuda.stream(self.stream):
-            pg.replay()
-            self.free[b].record(self.stream)
+            pg.replay_front()
+            self.gram_done.record(self.stream)
+            self.pg[0].replay_back()
             srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
             for dst, src in zip(self.host_out[b], srcs):
                 dst.copy_(src, non_blocking=True)

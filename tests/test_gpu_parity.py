@@ -75,6 +75,27 @@ def test_transform_bit_exact_f32(dp):
     assert np.array_equal(Q.cpu().numpy(), ref)
 
 
+def test_transform_bit_exact_at_the_ends_of_the_exponent_range(dp):
+    """Centred values around 2^+-900 (where the division switches between Markstein's correction
+    and the IEEE division), subnormals and mixed magnitudes: still the oracle's bits."""
+    rng = np.random.default_rng(900)
+    k = 23
+    big = np.ldexp(rng.uniform(1, 2, (40, k)) * rng.choice([-1, 1], (40, k)), rng.integers(880, 921, (40, 1)))
+    tiny = np.ldexp(rng.uniform(1, 2, (40, k)) * rng.choice([-1, 1], (40, k)), rng.integers(-930, -869, (40, 1)))
+    sub = rng.standard_normal((40, k)) * 1e-310
+    sub[:, ::3] = rng.standard_normal((40, (k + 2) // 3))
+    # rows of a unit-scale variable whose centred values sit around 2^-900
+    low = rng.standard_normal((40, k))
+    low[20:] = np.ldexp(rng.uniform(1, 2, (20, k)) * rng.choice([-1, 1], (20, k)), rng.integers(-905, -894, (20, 1)))
+    Qn = np.vstack([big, tiny, sub, low])
+    offs = [0, 40, 80, 120, 160]
+    Q = to_dev(dp, Qn)
+    mean, scale, _ = dp.dopinf_transform(Q, offs)
+    ref, rmean, rscale, _ = O.transform(Qn, offs)
+    assert np.array_equal(scale.cpu().numpy(), rscale)
+    assert np.array_equal(Q.cpu().numpy(), ref)
+
+
 def test_transform_zero_scale_and_nonfinite(dp):
     Qn = np.ones((64, 5))
     Qn[32:] = np.arange(5.0)
