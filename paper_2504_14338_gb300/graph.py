@@ -173,12 +173,12 @@ class StreamingPipeline:
 
     Two device copies of the snapshot matrix, each with its own captured front graph
     (transform and Gram, the steps that read the matrix); reduce and learn form one shared back
-    graph (the workspaces and outputs are shared).  The next matrix is uploaded into the other
-    copy on a copy stream once the current step's Gram has finished, so the transfer hides behind
-    the reduce and learn steps and its writes do not pass through L2 while the Gram's digit
-    planes live there.  Each step's results (training errors, statuses, the best index and its
-    operators, the failure flags) are copied back into pinned host memory on the compute
-    stream; result(i) waits for step i's copy and returns them.
+    graph (the workspaces and outputs are shared).  The upload of a matrix into a copy waits only
+    for the front graph that last read that copy (two steps back), so it runs on its copy stream
+    alongside the previous step (measured: such uploads do not slow the compute).  Each step's
+    results (training errors, statuses, the best index and its operators, the failure flags) are
+    copied back into pinned host memory on the compute stream; result(i) waits for step i's copy
+    and returns them.
     """
 
     OUTS = ("train_err", "status", "best", "O_best")
@@ -203,10 +203,11 @@ class StreamingPipeline:
         torch.cuda.synchronize(dev)
         self.stream = torch.cuda.Stream(device=dev)
         self.copy_stream = torch.cuda.Stream(device=dev)
-        self.gram_done = torch.cuda.Event()                      # the last queued front graph finished
-        self.uploaded = [torch.cuda.Event() for _ in range(2)]  # QT[b] holds the next matrix
-        self.fetched = [torch.cuda.Event() for _ in range(2)]   # host slot b holds a step's results
-        self.gram_done.record(torch.cuda.current_stream(dev))
+        self.front_done = [torch.cuda.Event() for _ in range(2)]  # the last front graph on QT[b] finished
+        self.uploaded = [torch.cuda.Event() for _ in range(2)]    # QT[b] holds the next matrix
+        self.fetched = [torch.cuda.Event() for _ in range(2)]     # host slot b holds a step's results
+        for e in self.front_done:
+            e.record(torch.cuda.current_stream(dev))
         pg = self.pg[0]
         srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
         self.host_out = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in srcs] for _ in range(2)]
@@ -218,16 +219,15 @@ class StreamingPipeline:
         """Queue one step on host_QT (pinned, the shape of the first); returns its index."""
         i, b = self.count, self.count % 2
         pg = self.pg[b]
-        # the upload into copy b waits for the last queued Gram (step i - 1's, which also
-        # follows step i - 2's, the last reader of copy b)
-        self.copy_stream.wait_event(self.gram_done)
+        # the upload into copy b waits for the front graph that last read it (step i - 2)
+        self.copy_stream.wait_event(self.front_done[b])
         with torch.cuda.stream(self.copy_stream):
             self.QT[b].copy_(host_QT, non_blocking=True)
             self.uploaded[b].record(self.copy_stream)
         self.stream.wait_event(self.uploaded[b])
         with torch.cuda.stream(self.stream):
             pg.replay_front()
-            self.gram_done.record(self.stream)
+            self.front_done[b].record(self.stream)
             self.pg[0].replay_back()
             srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
             for dst, src in zip(self.host_out[b], srcs):
