@@ -603,6 +603,12 @@ def main():
                 "stages_ms": stage, "pipeline_gram": args.pipeline_gram, "gram_useful_tflops": gram_tf,
                 "gram_modes": modes, "learn_s": stage["learn"] / 1e3,
                 "best": {"index": best, "r": res.get("r"), "beta1": res.get("beta1"), "beta2": res.get("beta2")},
+                "arithmetic": {"transform": "f64 (bit-exact)",
+                               "gram": ("exact integer digit products on the BF16 tensor cores, FP64-accurate"
+                                        if args.pipeline_gram == "ozaki" else "f64"),
+                               "reduce": "f64", "learn_solves": "f64",
+                               "rollouts": ("f32 double-word (~48 bits), statuses as in f64"
+                                            if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else "f64")},
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq}
         print(json.dumps(line), flush=True)
