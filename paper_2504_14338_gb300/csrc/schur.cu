@@ -102,6 +102,7 @@ __global__ void schur_potrf(const SchurUnit* __restrict__ units, int p0, int* __
 __global__ void __launch_bounds__(SB) schur_trsm(const SchurUnit* __restrict__ units, int p0,
                                                  const int* __restrict__ fail) {
   __shared__ double Lp[NB][NB + 1];
+  __shared__ double invd[NB];  // reciprocals of the diagonal: the sweep multiplies, no division on its chain
   const SchurUnit U = units[blockIdx.y];
   if (p0 >= U.s || fail[U.unit]) return;
   const int pw = panel_width(U.s, p0), N = U.N, q0 = p0 + pw;
@@ -112,6 +113,8 @@ __global__ void __launch_bounds__(SB) schur_trsm(const SchurUnit* __restrict__ u
     if (i < pw && j <= i) Lp[i][j] = E[(p0 + i) + (int64_t)(p0 + j) * N];
   }
   __syncthreads();
+  if (threadIdx.x < pw) invd[threadIdx.x] = 1.0 / Lp[threadIdx.x][threadIdx.x];
+  __syncthreads();
   const int row = q0 + (int)blockIdx.x * SB + threadIdx.x;
   if (row >= N) return;
   double x[NB];
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(SB) schur_trsm(const SchurUnit* __restrict__ u
       double v = E[row + (int64_t)(p0 + j) * N];
 #pragma unroll
       for (int l = 0; l < j; ++l) v = fma(-x[l], Lp[j][l], v);
-      x[j] = v / Lp[j][j];
+      x[j] = v * invd[j];
     }
   }
 #pragma unroll
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(SB) schur_update(const SchurUnit* __restrict__
 // m + r columns c; one thread per column.
 __global__ void schur_back_diag(const SchurUnit* __restrict__ units, int p0, const int* __restrict__ fail) {
   __shared__ double Lp[NB][NB + 1];
+  __shared__ double invd[NB];  // reciprocals of the diagonal: the sweep multiplies
   const SchurUnit U = units[blockIdx.x];
   if (p0 >= U.s || fail[U.unit]) return;
   const int pw = panel_width(U.s, p0), N = U.N, s = U.s, nc = U.m + U.r;
@@ -197,6 +201,8 @@ __global__ void schur_back_diag(const SchurUnit* __restrict__ units, int p0, con
     const int i = e % NB, j = e / NB;
     if (i < pw && j <= i) Lp[i][j] = E[(p0 + i) + (int64_t)(p0 + j) * N];
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < pw; j += blockDim.x) invd[j] = 1.0 / Lp[j][j];
   __syncthreads();
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     double x[NB];
@@ -207,7 +213,7 @@ __global__ void schur_back_diag(const SchurUnit* __restrict__ units, int p0, con
 #pragma unroll
         for (int l = jj + 1; l < NB; ++l)
           if (l < pw) v = fma(-Lp[l][jj], x[l], v);
-        x[jj] = v / Lp[jj][jj];
+        x[jj] = v * invd[jj];
       }
     }
 #pragma unroll
