@@ -476,9 +476,9 @@ def main():
         h2d_gbs = host_raw.numel() * host_raw.element_size() / (min(up) / 1e3) / 1e9
         sp = StreamingPipeline(host_raw, offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt,
                                gram_mode=pipe_mode, device=dev)
-        sp.run([host_raw] * max(1, args.warmup))
+        sp.run([host_raw] * max(2, args.warmup))
         torch.cuda.synchronize()
-        n_e2e = max(2, args.steps)
+        n_e2e = max(6, args.steps)
         if world > 1:
             dist.barrier()
         s0 = time.perf_counter()
