@@ -595,6 +595,26 @@ def main():
     if rank == 0 and not args.no_sequential:
         seq_ms = sequential_learn_measure(dp, red_last["Qhat"], w, mode)
         seq = {"sequential_ms": seq_ms, "batched_ms": stage["learn"], "speedup": seq_ms / stage["learn"]}
+    # the learn step once more with FP64 rollouts, for reading the default double-word ones
+    # against (time, selected candidate, training errors of the valid candidates)
+    fp64_roll = None
+    if rank == 0 and not args.no_sequential:
+        prev = dp.dopinf_tune_rollout_arith(dp.ROLLOUT_FP64)
+        try:
+            for _ in range(2):
+                r64 = dp.dopinf_learn(red_last["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode,
+                                      dt=w.snap_dt, ws=ws)
+            e_dw, e64 = res["train_err"].cpu().numpy(), r64["train_err"].cpu().numpy()
+            ok = np.isfinite(e64) & np.isfinite(e_dw)
+            fp64_roll = {"rollouts_ms": r64["stage_ms"]["rollouts"], "best": r64["best"],
+                         "same_best": r64["best"] == res["best"],
+                         "same_status": bool(np.array_equal(r64["status"].cpu().numpy(), res["status"].cpu().numpy())),
+                         "max_rel_train_err_diff_valid": float(np.max(np.abs(e_dw[ok] - e64[ok]) / e64[ok])) if ok.any()
+                         else None}
+        except Exception as ex:  # reported, never fatal for the line
+            fp64_roll = {"error": str(ex)}
+        finally:
+            dp.dopinf_tune_rollout_arith(prev)
     if rank == 0:
         best = res["best"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -610,7 +630,8 @@ def main():
                                "rollouts": ("f32 double-word (~48 bits), statuses as in f64"
                                             if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else "f64")},
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
-                "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq}
+                "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq,
+                "learn_fp64_rollouts": fp64_roll}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
