@@ -10,9 +10,12 @@
 //   train_stats     temporal mean mu of the reference and max_{t<k,i} |qhat - mu|;
 // Then schur_solve (schur.cu) solves (G + diag(reg)) O^T = B for every (r, beta1, beta2) by
 // block elimination of the quadratic unknowns, shared across beta1, and the rollouts run every
-// candidate (a thread-block cluster each) with the fused training error / growth epilogue.
-// Then select_best takes the lowest training error among valid candidates (lowest index on
-// ties).  Everything is FP64.
+// candidate (a thread-block cluster each; rollout.cu) with the fused training error / growth
+// epilogue: for r <= 32 one launch per r, largest first, chained by programmatic dependent
+// launch so that they run side by side, in the arithmetic set by dopinf_tune_rollout_arith
+// (double-word FP32 by default, with an FP64 pass over the candidates it hands back).  Then
+// select_best takes the lowest training error among valid candidates (lowest index on ties).
+// Everything else is FP64.
 #include "common.cuh"
 
 #include <algorithm>

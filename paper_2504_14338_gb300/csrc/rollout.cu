@@ -1,8 +1,12 @@
 // Rollouts of learned quadratic ROMs (Section 3.5): the discrete map of
 // eq. ROM_quad_time_discrete, or classical RK4 on eq. ROM_quad_time_cont, with the training
-// error and growth criterion of Step IV fused into the time loop.
+// error and growth criterion of Step IV fused into the time loop.  Two kernels:
+//  * rollout_cols_kernel (below, r <= 32, the path of the workloads): column-owned layout,
+//    one launch per r, FP64 or double-word FP32 arithmetic;
+//  * rollout_kernel (r > 32): the row-split layout described here.
 //
-// One thread-block cluster of C CTAs per candidate, every candidate of every r in one launch.
+// Row-split kernel: one thread-block cluster of C CTAs per candidate, every candidate of every r
+// in one launch.
 // CTA rank j of the cluster keeps rows [j*rc, (j+1)*rc) of the operator O = [A | H | c]
 // (rc = ceil(r / C)) row-major in its shared memory.  Each right-hand-side evaluation builds
 // phi = [q, (q_i q_j)_{i<=j}, 1] locally (the state is replicated), forms its rows of O phi

@@ -1,4 +1,6 @@
-"""The whole hot path (Steps II-IV) captured once into a CUDA graph and replayed.
+"""The whole hot path (Steps II-IV) captured once into a CUDA graph and replayed
+(PipelineGraph); matrices streamed from pinned host memory with overlapped uploads
+(StreamingPipeline); many learn problems in one graph (BatchedLearnGraph).
 
 Every buffer is allocated up front; capture records the asynchronous entry points
 (dopinf_transform, dopinf_gram_async, dopinf_reduce_async, dopinf_learn_async), which neither
