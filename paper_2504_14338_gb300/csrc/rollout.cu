@@ -733,8 +733,11 @@ bool cluster_fits(void* fn, int c) {
   const auto key = std::make_pair(fn, c);
   const auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  bool ok = true;
-  if (c > 8) ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  bool ok = true, refused = false;
+  if (c > 8) {
+    ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    refused = !ok;
+  }
   if (ok) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c, 1, 1);
@@ -747,9 +750,13 @@ bool cluster_fits(void* fn, int c) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    ok = cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1;
+    const cudaError_t q = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+    refused = refused || q != cudaSuccess;
+    ok = q == cudaSuccess && n >= 1;
   }
-  cudaGetLastError();  // a refused size is an answer, not an error to report later
+  // a refused size is an answer, not an error to report later: clear the error this query
+  // raised (and only then, so that no earlier error of the caller's is swallowed)
+  if (refused) cudaGetLastError();
   cache[key] = ok;
   return ok;
 }
