@@ -164,9 +164,15 @@ int dopinf_gram_async(const void* Q, int dtype, int64_t n, int64_t k, int64_t ld
  * (dopinf_gram_noalloc_scratch_bytes() returns the size).
  *  - Limit: k <= 2816 (the 64 x 64 upper tiles of D must fit the array); larger k returns
  *    DOPINF_E_UNSUPPORTED before anything is launched.  n >= 1.
- *  - The first call on each device resolves the array's device address on that device
- *    (the device must be current); make that first call before any stream capture, and not
- *    from several host threads at once.
+ *  - The array is reserved when the driver loads this library's code on a device, which
+ *    (under lazy module loading, the CUDA default) happens at the first call of this entry
+ *    point or of any other library call that runs the FP64 Gram kernels on that device.
+ *    That first use therefore does allocate device memory: make it outside any code that
+ *    must not allocate (for example, once at start-up).
+ *  - The first call on each device (the device must be current), and the first call after
+ *    that device's context was replaced (cudaDeviceReset), resolve the array's device
+ *    address; make that call before any stream capture, and not from several host threads
+ *    at once.  Later calls only compare the context id.
  *  - Every call on a device shares the one array and leaves its last contents there; calls
  *    that overlap on the GPU (different streams, no ordering between them) race on it and
  *    give wrong results.  Calls on one stream are safe.  Asynchronous; D follows the same

@@ -242,10 +242,45 @@ constexpr int kNoAllocMaxUnits = (int)(kNoAllocScratchBytes / (TM * TN * sizeof(
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
 
 constexpr int kNoAllocMaxDevices = 128;
-// Device address of g_noalloc_scratch per device ordinal.  In host code the symbol name is a
-// host-side stand-in, not a device address, so it is resolved once per device with
-// cudaGetSymbolAddress while that device is current.
-void* g_noalloc_addr[kNoAllocMaxDevices];
+constexpr int kNoAllocMaxK = 2816;  // 44 x 44 tiles of 64: 990 upper tiles of 32 KB fit the array
+static_assert((kNoAllocMaxK / TM) * (kNoAllocMaxK / TM + 1) / 2 <= kNoAllocMaxUnits, "k limit");
+
+// Device address of g_noalloc_scratch per device ordinal, with the id of the context it was
+// resolved in.  In host code the symbol name is a host-side stand-in, not a device address,
+// so it is resolved with cudaGetSymbolAddress while the device is current, and again whenever
+// the device's context has changed (after a cudaDeviceReset the array may sit elsewhere).
+struct NoAllocAddr {
+  void* addr;
+  unsigned long long ctx_id;
+};
+NoAllocAddr g_noalloc_addr[kNoAllocMaxDevices];
+
+// Id of the calling thread's current context (0 if none is current yet), through the driver
+// entry points the runtime hands out, so that the library does not link libcuda itself.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();  // a missing entry point only disables the check
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 }  // namespace
 }  // namespace dopinf
@@ -257,9 +292,10 @@ DOPINF_API int dopinf_gram_fp64_noalloc(const void* Q, int dtype, int64_t n, int
   using namespace dopinf;
   if (n < 1 || k < 1 || ldq < n || ldd < k || !D || !Q) return DOPINF_E_ARG;
   if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
+  if (k > kNoAllocMaxK) return DOPINF_E_UNSUPPORTED;  // before any tile count is formed
   // plan: as the workspace path, with the row split reduced until the partials fit the array
   TnPlan p = make_plan(n, k, k, 1);
-  if (p.ntiles > kNoAllocMaxUnits) return DOPINF_E_UNSUPPORTED;  // k too large for the fixed scratch
+  if (p.ntiles > kNoAllocMaxUnits) return DOPINF_E_UNSUPPORTED;
   if (p.units > kNoAllocMaxUnits) {
     const int splits = kNoAllocMaxUnits / p.ntiles;
     int64_t rps = (n + splits - 1) / splits;
@@ -272,12 +308,16 @@ DOPINF_API int dopinf_gram_fp64_noalloc(const void* Q, int dtype, int64_t n, int
   int dev = 0;
   DOPINF_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return DOPINF_E_UNSUPPORTED;
-  if (!g_noalloc_addr[dev]) {  // first call on this device: resolve the array's device address
+  // first call on this device, or a new context since the address was taken: resolve it
+  NoAllocAddr& slot = g_noalloc_addr[dev];
+  const unsigned long long ctx = current_ctx_id();
+  if (!slot.addr || ctx == 0 || ctx != slot.ctx_id) {
     void* addr = nullptr;
     DOPINF_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
-    g_noalloc_addr[dev] = addr;
+    slot.addr = addr;
+    slot.ctx_id = ctx ? ctx : current_ctx_id();  // the lookup above made the context current
   }
-  double* part = static_cast<double*>(g_noalloc_addr[dev]);
+  double* part = static_cast<double*>(slot.addr);
   cudaStream_t st = as_stream(stream);
   if (dtype == DOPINF_F64)
     tn_partial<double><<<p.grid, NT, 0, st>>>(static_cast<const double*>(Q), ldq, static_cast<const double*>(Q), ldq,

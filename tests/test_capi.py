@@ -78,6 +78,14 @@ def test_arguments_rejected_before_launch():
     rl4 = (ctypes.c_int * 1)(4)
     assert L.dopinf_learn(p8, 3, 50, 3, rl4, 1, b, 1, b, 1, 0, 1.0, 100, 1.2, p8, p8, p8, z, ctypes.byref(best), p8,
                           None, p8, 1 << 30, z) == dp.E_ARG
+    # allocation-free Gram: k beyond its fixed array is refused before any tile count or CUDA call
+    f = L.dopinf_gram_fp64_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    for k in (2817, 5_000_000, 1 << 40):
+        assert f(p8, 0, 64, k, 64, 0, p8, k, z) == dp.E_UNSUPPORTED, k
+    assert f(p8, 0, 64, 100, 63, 0, p8, 100, z) == dp.E_ARG      # ldq < n
     # rollout: r = 0, ldo < r
     assert L.dopinf_rollout(p8, 0, 1, p8, 10, 0, 1.0, p8, p8, z) == dp.E_ARG
     assert L.dopinf_rollout(p8, 3, 2, p8, 10, 0, 1.0, p8, p8, z) == dp.E_ARG

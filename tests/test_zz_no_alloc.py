@@ -56,6 +56,23 @@ def test_noalloc_gram_matches_workspace_gram_twice(dp, n, k, dtype):
         assert bool(torch.equal(D, D.t()))
 
 
+def test_noalloc_accumulate_adds_row_blocks_twice(dp):
+    """accumulate = 1 adds Q^T Q of each row block to D, like the workspace entry point does."""
+    n, k = 30_000, 200
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    Q = torch.randn(k, n, generator=g, device="cuda", dtype=torch.float64).t()
+    ref = dp.dopinf_gram(Q)
+    diag = torch.diagonal(ref).abs()
+    bound = 8 * np.sqrt(n) * EPS * torch.sqrt(torch.outer(diag, diag))
+    for _ in range(2):
+        D = torch.zeros(k, k, dtype=torch.float64, device="cuda")
+        for a, b in [(0, 10_000), (10_000, 20_000), (20_000, n)]:
+            assert _noalloc(dp, Q[a:b], D, accumulate=1) == dp.OK
+        torch.cuda.synchronize()
+        assert bool(torch.all(torch.abs(D - ref) <= bound))
+
+
 def test_noalloc_rejects_k_beyond_the_fixed_scratch(dp):
     Q = torch.zeros(2900, 64, dtype=torch.float64, device="cuda").t()   # n = 64, k = 2900
     D = torch.zeros(2900, 2900, dtype=torch.float64, device="cuda")
