@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch schedules")
     p.add_argument("--n-steps", type=int, default=0, help="override the rollout length of --stage learn")
     p.add_argument("--r-list", default="", help="override the r list of --stage learn, e.g. 30 or 10,20")
-    p.add_argument("--cluster", type=int, default=0, help="--stage learn: rollout cluster size (1, 2, 4, 8; 0: default)")
+    p.add_argument("--rows-large", type=int, default=0, help="--stage learn: rollout rows per CTA for r > 32 (3..8; 0: default)")
     return p.parse_args()
 
 
@@ -353,8 +353,8 @@ def main():
     if args.stage == "learn":
         r_list = [int(x) for x in args.r_list.split(",")] if args.r_list else list(w.r_list)
         n_steps = args.n_steps or w.n_steps
-        if args.cluster:
-            dp.dopinf_tune_learn_cluster(args.cluster)
+        if args.rows_large:
+            dp.dopinf_tune_rollout_rows_large(args.rows_large)
         dp.dopinf_transform(Q, offs, ws=ws)
         red = dp.dopinf_reduce(dp.dopinf_gram(Q, ws=ws), r_cap=r_max, r_fixed=r_max, ws=ws)
         times = []
@@ -370,7 +370,7 @@ def main():
         if rank == 0:
             print(json.dumps({"stage": "learn", "ms": float(np.mean(times)), "best": res["best"],
                               "valid": int((st == 0).sum()), "n_cand": int(st.size), "r_list": r_list,
-                              "n_steps": n_steps, "cluster": args.cluster}), flush=True)
+                              "n_steps": n_steps, "rows_large": args.rows_large}), flush=True)
         return
 
     last = {}

@@ -68,12 +68,13 @@ enum dopinf_rom_mode {
   DOPINF_CONTINUOUS_RK4 = 1  /* q' = A q + H (q x q)_u + c, central-difference derivatives, RK4 rollout */
 };
 
-/* Arithmetic of the rollouts of r <= 32 inside dopinf_learn / dopinf_learn_async (dopinf_rollout
- * always uses FP64): binary64, or double-word binary32 pairs (about 48 significant bits, on the
- * FP32 pipe) with compensated dot products.  Double-word candidates whose operator or initial
- * state exceed 2^60 in magnitude, or whose state stops being finite, are rolled out again in
- * FP64, so statuses and step counts follow the FP64 arithmetic; train_err and growth agree with
- * it to rounding of order 1e-13 relative for stable rollouts. */
+/* Arithmetic of the rollouts inside dopinf_learn / dopinf_learn_async (dopinf_rollout always
+ * uses FP64): binary64, or double-word binary32 pairs (about 48 significant bits, on the FP32
+ * pipe) with compensated dot products.  Double-word candidates whose operator or initial state
+ * exceed 2^60 in magnitude, whose state stops being finite, or whose growth comes within 2^-20
+ * (relative) of max_growth are rolled out again in FP64, so statuses and step counts follow the
+ * FP64 arithmetic; train_err and growth agree with it to rounding of order 1e-12 relative for
+ * stable rollouts. */
 enum dopinf_rollout_arith {
   DOPINF_ROLLOUT_FP64 = 1,
   DOPINF_ROLLOUT_DW = 2
@@ -223,8 +224,8 @@ int dopinf_tune_reduce_coop(int on);
  * OpInf_data_matrices_discrete; the training error and growth criterion of Step IV).
  *
  * Qhat       r_max x k reduced data (ld ldqh >= r_max), column t = snapshot t.
- * r_list     host, n_r reduced dimensions (1 <= r <= r_max, k-1 (discrete) or k-2
- *            (continuous) rows of data are used).
+ * r_list     host, n_r reduced dimensions (1 <= r <= r_max, r <= 92 (DOPINF_E_UNSUPPORTED
+ *            above); k-1 (discrete) or k-2 (continuous) rows of data are used).
  * beta1, beta2  host, n_b1 and n_b2 regularisation values.
  * Candidates are numbered r-major, then beta1, then beta2:
  *   c = (ir * n_b1 + i1) * n_b2 + i2.
@@ -254,17 +255,18 @@ int dopinf_tune_reduce_coop(int on);
  * n_b1, n_b2 <= 64 (DOPINF_E_UNSUPPORTED above).
  * Workspace: dopinf_learn_workspace(...) bytes.
  * ------------------------------------------------------------------------------------ */
-/* Tuning of the row-split rollouts, used when some r of the list is above 32: preferred CTAs
- * (1, 2, 4 or 8) of the thread-block cluster that rolls out one candidate of r >= 16 (default
- * 4); other values only query.  Returns the previous value.  Process-wide. */
-int dopinf_tune_learn_cluster(int cluster);
 /* Tuning of the rollouts of r <= 32 (dopinf_learn, dopinf_learn_async, dopinf_rollout): rows
  * of O per CTA, 1, 2 or 4 (default 4; raised where the cluster of ceil(r / rows) CTAs would
  * exceed 16 or cannot be resident); other values only query.  Returns the previous value.
  * Process-wide.  The results do not depend on it. */
 int dopinf_tune_rollout_rows(int rows);
-/* Rollout arithmetic of dopinf_learn for r <= 32: DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW
- * (default); other values only query.  Returns the previous value.  Process-wide. */
+/* The same for the rollouts of 32 < r <= 92 (operator rows in shared memory): rows of O per
+ * CTA, 3 to 8 (default 4; raised where the cluster would exceed 16 CTAs or cannot be
+ * resident); other values only query.  Returns the previous value.  Process-wide.  The
+ * results do not depend on it. */
+int dopinf_tune_rollout_rows_large(int rows);
+/* Rollout arithmetic of dopinf_learn: DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW (default); other
+ * values only query.  Returns the previous value.  Process-wide. */
 int dopinf_tune_rollout_arith(int arith);
 size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1,
                               int n_b2);
@@ -273,6 +275,14 @@ int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
                  int mode, double dt, int64_t n_steps, double max_growth, double* train_err,
                  double* growth, int* cand_status, int64_t* cand_steps, int* best_out,
                  double* O_best, double* stage_ms, void* ws, size_t ws_bytes, void* stream);
+
+/* Every candidate's operators: after dopinf_learn or dopinf_learn_async has run with this grid
+ * (k, r_list, n_b1, n_b2) and workspace, and until the workspace is reused, candidate cand's
+ * O = [A | H | c] (r x d doubles, column-major, ld r, r = its reduced dimension) lies at this
+ * byte offset from the start of the workspace.  Its contents are meaningful where the
+ * candidate's Cholesky factorisation succeeded (cand_status != 1).  Host-only query;
+ * (size_t)-1 for bad arguments. */
+size_t dopinf_learn_operator_offset(int64_t k, const int* r_list, int n_r, int n_b1, int n_b2, int cand);
 
 /* The same without synchronisation and without host copies (capturable into a CUDA graph;
  * the candidate tables are built on the device): best_dev (device int, required) receives the

@@ -3,10 +3,9 @@
 Two knobs decide how the work is laid out on the GPU without changing a single bit of the
 results (both choices are exercised by the GPU tests):
 
-* how many operator rows each CTA of a rollout cluster owns (1, 2 or 4, so ceil(r / rows) CTAs
-  per candidate; or, for r above 32, the cluster size 1, 2, 4 or 8 of the row-split kernel):
-  large clusters shorten each candidate's chain of evaluations, small ones leave more of the
-  GPU's FP64 issue to the other candidates;
+* how many operator rows each CTA of a rollout cluster owns (1, 2 or 4 for r <= 32, 3 to 8 for
+  r above 32, so ceil(r / rows) CTAs per candidate): large clusters shorten each candidate's
+  chain of evaluations, small ones leave more of the GPU's issue slots to the other candidates;
 * the Householder tridiagonalisation as one cooperative launch (a grid barrier per column) or
   as three launches per column.
 
@@ -35,39 +34,48 @@ def _key(kind, *parts):
     return (kind, torch.cuda.get_device_name(), *parts)
 
 
-def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, clusters=(1, 2, 4, 8), rows=(1, 2, 4),
-               reps=3, ws=None, timer=None):
+def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, rows=(1, 2, 4),
+               rows_large=(3, 4, 5, 6, 8), reps=3, ws=None, timer=None):
     """Time the rollouts of this grid search for each launch shape; set and return the best.
 
-    Every r <= 32: operator rows per CTA of the column-owned rollouts (`rows`); otherwise the
-    cluster size of the row-split rollouts (`clusters`).  timer(setting) -> milliseconds
-    replaces the measurement (host-logic tests)."""
-    cols = max(int(r) for r in r_list) <= 32
-    setter = dp.dopinf_tune_rollout_rows if cols else dp.dopinf_tune_learn_cluster
-    settings = rows if cols else clusters
+    Two knobs, tuned one after the other (the other one held at its current value): operator
+    rows per CTA of the rollouts of r <= 32 (`rows`) if the list has such an r, and of the
+    rollouts of r > 32 (`rows_large`) if it has such an r.  timer(knob, setting) ->
+    milliseconds replaces the measurement (host-logic tests).  The result names the first
+    knob tuned ("knob", "best", "rollout_ms") and lists all of them under "knobs"."""
+    knobs = []
+    if min(int(r) for r in r_list) <= 32:
+        knobs.append(("rollout rows per CTA", dp.dopinf_tune_rollout_rows, rows))
+    if max(int(r) for r in r_list) > 32:
+        knobs.append(("rollout rows per CTA (r > 32)", dp.dopinf_tune_rollout_rows_large, rows_large))
     key = _key("learn", tuple(r_list), len(beta1), len(beta2), int(n_steps), int(mode), int(Qhat.shape[1]))
     if timer is None and key in _cache:
-        setter(_cache[key]["best"])
+        for (name, setter, _), k in zip(knobs, _cache[key]["knobs"]):
+            setter(k["best"])
         return _cache[key]
-    prev = setter(0)
-    times = {}
-    try:
-        for c in settings:
-            if timer is not None:
-                times[c] = float(timer(c))
-                continue
-            setter(c)
-            best_ms = None
-            for _ in range(reps + 1):  # the first run warms up
-                res = dp.dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=mode, dt=dt, ws=ws)
-                ms = res["stage_ms"]["rollouts"]
-                best_ms = ms if best_ms is None else min(best_ms, ms)
-            times[c] = best_ms
-    finally:
-        setter(prev)
-    best = pick_fastest(times)
-    setter(best)
-    out = {"knob": "rollout rows per CTA" if cols else "rollout cluster size", "best": best, "rollout_ms": times}
+    results = []
+    for name, setter, settings in knobs:
+        prev = setter(0)
+        times = {}
+        try:
+            for c in settings:
+                if timer is not None:
+                    times[c] = float(timer(name, c))
+                    continue
+                setter(c)
+                best_ms = None
+                for _ in range(reps + 1):  # the first run warms up
+                    res = dp.dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=mode, dt=dt, ws=ws)
+                    ms = res["stage_ms"]["rollouts"]
+                    best_ms = ms if best_ms is None else min(best_ms, ms)
+                times[c] = best_ms
+        finally:
+            setter(prev)
+        best = pick_fastest(times)
+        setter(best)
+        results.append({"knob": name, "best": best, "rollout_ms": times})
+    out = dict(results[0])
+    out["knobs"] = results
     if timer is None:
         _cache[key] = out
     return out

@@ -125,7 +125,7 @@ struct RolloutCand {
 struct RolloutBatch {
   const RolloutCand* cands;  // device table of n_cand candidates, or nullptr to use `one`
   RolloutCand one;
-  int n_cand, r_max, d_max, rc_max;
+  int n_cand, r_max, d_max;
   int mode;
   double dt;
   int64_t n_steps;
@@ -144,27 +144,31 @@ struct RolloutBatch {
   int traj;
   double* traj_out;
   int* finite;
-  // column-owned kernel (r <= 32): arithmetic (DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW), and
-  // redo = 1 for the FP64 pass over the candidates a double-word pass handed back (status 4)
+  // arithmetic (DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW), and redo = 1 for the FP64 pass over
+  // the candidates a double-word pass handed back (status 4)
   int arith;
   int redo;
 };
 
-size_t rollout_smem_bytes(int cluster, int r_max, int d_max);
-// Cluster size in {1, 2, 4, 8}, at least `want`, with the operator slice in shared memory; 0 if none fits.
-int rollout_cluster_size(int r_max, int d_max, int want);
-int launch_rollouts(RolloutBatch bt, int cluster, cudaStream_t st);
-// Column-owned rollouts (r <= 32): whether r is supported, the rows per CTA and cluster size a
-// launch for r would use (0 if none fits), the process-wide preferred rows per CTA (1, 2, 4;
-// other values only query; returns the previous value), and the launch of candidates
-// [cand0, cand0 + n) of one r (chained: programmatic dependent launch behind the previous
-// rollout launch on the stream, which it completes after).
+// Rollouts (rollout.cu).  Column-owned kernel for r <= 32: whether r is supported, the rows per
+// CTA and cluster size a launch for r would use (0 if none fits), the process-wide preferred
+// rows per CTA (1, 2, 4; other values only query; returns the previous value), and the launch
+// of candidates [cand0, cand0 + n) of one r (chained: programmatic dependent launch behind the
+// previous rollout launch on the stream, which it completes after).  Shared-memory kernel for
+// 32 < r <= 92: the same, with preferred rows per CTA 3..8.
 bool rollout_cols_supported(int r);
 int rollout_cols_shape(int r, int* rows, int* cluster);
 int rollout_set_rows(int rc);
+int launch_rollouts_cols(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st);
+bool rollout_big_supported(int r);
+int rollout_big_shape(int r, int* rows, int* cluster, size_t* smem);
+int rollout_set_rows_big(int rc);
+int launch_rollouts_big(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st);
+// Either kernel, chosen by r.
+bool rollout_supported(int r);
+int rollout_shape(int r);
+int launch_rollouts_rank(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st);
 int rollout_set_arith(int a);
 int rollout_arith();
-int launch_rollouts_cols(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st);
-int learn_set_cluster(int c);
 
 }  // namespace dopinf

@@ -11,9 +11,9 @@
 // Then schur_solve (schur.cu) solves (G + diag(reg)) O^T = B for every (r, beta1, beta2) by
 // block elimination of the quadratic unknowns, shared across beta1, and the rollouts run every
 // candidate (a thread-block cluster each; rollout.cu) with the fused training error / growth
-// epilogue: for r <= 32 one launch per r, largest first, chained by programmatic dependent
-// launch so that they run side by side, in the arithmetic set by dopinf_tune_rollout_arith
-// (double-word FP32 by default, with an FP64 pass over the candidates it hands back).  Then
+// epilogue: one launch per r, largest first, chained by programmatic dependent launch so that
+// they run side by side, in the arithmetic set by dopinf_tune_rollout_arith (with double-word
+// FP32, an FP64 pass over the candidates it hands back follows).  Then
 // select_best takes the lowest training error among valid candidates (lowest index on ties).
 // Everything else is FP64.
 #include "common.cuh"
@@ -103,6 +103,7 @@ struct LearnWs {
   RolloutCand* roll;
   double *mu, *denom, *Dh, *Y;
   double *G[kMaxR], *B[kMaxR], *E[kMaxR], *S[kMaxR], *O[kMaxR];
+  size_t O_off[kMaxR];  // byte offset of O[i] in the workspace
   int r_stride;  // largest r of the list: stride of the per-r vectors (mu)
   int *best, *unit_fail;
   void* tn;
@@ -135,6 +136,7 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1,
     w.B[i] = c.take<double>(d * r);
     w.E[i] = c.take<double>((size_t)n_b2 * schur_unit_doubles((int)r));
     w.S[i] = c.take<double>((size_t)n_pairs * schur_cand_doubles((int)r));
+    w.O_off[i] = c.used;
     w.O[i] = c.take<double>((size_t)n_pairs * r * d);
   }
   size_t tb = 0;
@@ -150,16 +152,7 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1,
   return w;
 }
 
-int g_cluster_want = 4;  // tunable: preferred CTAs per candidate in the rollouts
-
 }  // namespace
-
-int learn_set_cluster(int c) {
-  const int prev = g_cluster_want;
-  if (c == 1 || c == 2 || c == 4 || c == 8) g_cluster_want = c;
-  return prev;
-}
-
 }  // namespace dopinf
 
 using namespace dopinf;
@@ -170,6 +163,18 @@ DOPINF_API size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list
   (void)r_max;
   if (!r_list || n_r < 1 || n_r > kMaxR || n_b1 < 1 || n_b2 < 1 || k < 3) return 0;
   return carve_learn(nullptr, k - 1, r_list, n_r, n_b1, n_b2).used;
+}
+
+DOPINF_API size_t dopinf_learn_operator_offset(int64_t k, const int* r_list, int n_r, int n_b1, int n_b2, int cand) {
+  if (!r_list || n_r < 1 || n_r > kMaxR || n_b1 < 1 || n_b2 < 1 || k < 3) return (size_t)-1;
+  const int n_pairs = n_b1 * n_b2;
+  if (cand < 0 || cand >= n_r * n_pairs) return (size_t)-1;
+  for (int i = 0; i < n_r; ++i)
+    if (r_list[i] < 1 || r_list[i] > 255) return (size_t)-1;
+  const LearnWs w = carve_learn(nullptr, k - 1, r_list, n_r, n_b1, n_b2);
+  const int ir = cand / n_pairs, p = cand % n_pairs;
+  const size_t r = r_list[ir], d = dim_d(r_list[ir]);
+  return w.O_off[ir] + (size_t)p * r * d * sizeof(double);
 }
 
 namespace dopinf {
@@ -246,11 +251,11 @@ __global__ void gather_best(const int* best, const SchurCand* cands, int r_max, 
   for (int e = threadIdx.x; e < r * d; e += blockDim.x) O_best[(e % r) + (size_t)(e / r) * r_max] = c.O[e];
 }
 
-// Checks of every argument; the rollout cluster size on success.
+// Checks of every argument; the largest r and d of the list on success.
 int learn_check(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
                 const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt, int64_t n_steps,
                 double max_growth, const double* train_err, const double* growth, const int* cand_status,
-                const double* O_best, void* ws, size_t ws_bytes, int* cluster, int* r_used, int* d_max) {
+                const double* O_best, void* ws, size_t ws_bytes, int* r_used, int* d_max) {
   if (!Qhat || r_max < 1 || ldqh < r_max || !r_list || n_r < 1 || n_r > kMaxR || !beta1 || !beta2 || n_b1 < 1 ||
       n_b2 < 1 || !train_err || !growth || !cand_status || !O_best)
     return DOPINF_E_ARG;
@@ -272,19 +277,10 @@ int learn_check(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const in
     if (!(beta2[i] >= 0.0)) return DOPINF_E_ARG;
   if (!ws || ws_bytes < dopinf_learn_workspace(r_max, k, r_list, n_r, n_b1, n_b2) || misaligned(ws))
     return DOPINF_E_ARG;
-  // rollouts: the column-owned kernel (one launch per r) when every r fits it, else the
-  // row-split kernel (cluster > 0) for all candidates in one launch
-  bool cols = true;
-  for (int i = 0; i < n_r && cols; ++i) {
-    int rc = 0, c = 0;
-    cols = rollout_cols_shape(r_list[i], &rc, &c) != 0;
-  }
-  if (cols) {
-    *cluster = -1;
-    return DOPINF_OK;
-  }
-  *cluster = rollout_cluster_size(*r_used, *d_max, *r_used >= 16 ? g_cluster_want : 1);
-  return *cluster ? DOPINF_OK : DOPINF_E_UNSUPPORTED;
+  // rollouts: every r must fit one of the two kernels (r <= 92)
+  for (int i = 0; i < n_r; ++i)
+    if (!rollout_supported(r_list[i]) || !rollout_shape(r_list[i])) return DOPINF_E_UNSUPPORTED;
+  return DOPINF_OK;
 }
 
 // The whole learn step on the stream, no synchronisation, no host copies.  ev (optional): 4
@@ -292,7 +288,7 @@ int learn_check(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const in
 int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const int* r_list, int n_r,
                  const double* beta1, int n_b1, const double* beta2, int n_b2, int mode, double dt, int64_t n_steps,
                  double max_growth, double* train_err, double* growth, int* cand_status, int64_t* cand_steps,
-                 int* best_dev, double* O_best, unsigned* dev_flags, int cluster, int r_used, int d_max, void* ws,
+                 int* best_dev, double* O_best, unsigned* dev_flags, int r_used, int d_max, void* ws,
                  cudaStream_t st, cudaEvent_t* ev) {
   const int64_t K = learn_rows(k, mode);
   // the workspace is laid out for K = k - 1 rows, which covers both modes
@@ -352,9 +348,7 @@ int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
   bt.growth = growth;
   bt.status = cand_status;
   bt.steps = cand_steps;
-  if (cluster > 0) {
-    DOPINF_TRY(launch_rollouts(bt, cluster, st));
-  } else {
+  {
     // one launch per r, largest r (longest evaluations) first; each later launch is chained
     // behind the one before by programmatic dependent launch, so all run side by side
     int order[kMaxR];
@@ -363,7 +357,7 @@ int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
     bt.arith = rollout_arith();
     for (int j = 0; j < n_r; ++j) {
       const int ir = order[j];
-      DOPINF_TRY(launch_rollouts_cols(bt, ir * n_pairs, n_pairs, r_list[ir], j > 0, st));
+      DOPINF_TRY(launch_rollouts_rank(bt, ir * n_pairs, n_pairs, r_list[ir], j > 0, st));
     }
     if (bt.arith == DOPINF_ROLLOUT_DW) {
       // the FP64 pass over whatever the double-word pass handed back (usually nothing: its
@@ -372,7 +366,7 @@ int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
       bt.redo = 1;
       for (int j = 0; j < n_r; ++j) {
         const int ir = order[j];
-        DOPINF_TRY(launch_rollouts_cols(bt, ir * n_pairs, n_pairs, r_list[ir], j > 0, st));
+        DOPINF_TRY(launch_rollouts_rank(bt, ir * n_pairs, n_pairs, r_list[ir], j > 0, st));
       }
     }
   }
@@ -391,11 +385,11 @@ DOPINF_API int dopinf_learn_async(const double* Qhat, int r_max, int64_t k, int6
                                   int* cand_status, int64_t* cand_steps, int* best_dev, double* O_best,
                                   unsigned* dev_flags, void* ws, size_t ws_bytes, void* stream) {
   if (!best_dev || !dev_flags) return DOPINF_E_ARG;
-  int cluster = 0, r_used = 0, d_max = 0;
+  int r_used = 0, d_max = 0;
   DOPINF_TRY(learn_check(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
-                         train_err, growth, cand_status, O_best, ws, ws_bytes, &cluster, &r_used, &d_max));
+                         train_err, growth, cand_status, O_best, ws, ws_bytes, &r_used, &d_max));
   return learn_launch(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
-                      train_err, growth, cand_status, cand_steps, best_dev, O_best, dev_flags, cluster, r_used, d_max,
+                      train_err, growth, cand_status, cand_steps, best_dev, O_best, dev_flags, r_used, d_max,
                       ws, as_stream(stream), nullptr);
 }
 
@@ -405,9 +399,9 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
                             int64_t* cand_steps, int* best_out, double* O_best, double* stage_ms, void* ws,
                             size_t ws_bytes, void* stream) {
   if (!best_out) return DOPINF_E_ARG;
-  int cluster = 0, r_used = 0, d_max = 0;
+  int r_used = 0, d_max = 0;
   DOPINF_TRY(learn_check(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
-                         train_err, growth, cand_status, O_best, ws, ws_bytes, &cluster, &r_used, &d_max));
+                         train_err, growth, cand_status, O_best, ws, ws_bytes, &r_used, &d_max));
   cudaStream_t st = as_stream(stream);
   // optional stage timings (CUDA events on this stream): data + normal equations, solves, rollouts
   cudaEvent_t ev[4] = {};
@@ -422,7 +416,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
     for (int i = 0; i < 4; ++i) DOPINF_CUDA(cudaEventCreate(&ev[i]));
   LearnWs w = carve_learn(ws, k - 1, r_list, n_r, n_b1, n_b2);
   DOPINF_TRY(learn_launch(Qhat, r_max, k, ldqh, r_list, n_r, beta1, n_b1, beta2, n_b2, mode, dt, n_steps, max_growth,
-                          train_err, growth, cand_status, cand_steps, nullptr, O_best, nullptr, cluster, r_used, d_max,
+                          train_err, growth, cand_status, cand_steps, nullptr, O_best, nullptr, r_used, d_max,
                           ws, st, stage_ms ? ev : nullptr));
   int best = -1;
   DOPINF_CUDA(cudaMemcpyAsync(&best, w.best, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -437,7 +431,7 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
   return best < 0 ? DOPINF_E_NO_STABLE : DOPINF_OK;
 }
 
-DOPINF_API int dopinf_tune_learn_cluster(int cluster) { return learn_set_cluster(cluster); }
+DOPINF_API int dopinf_tune_rollout_rows_large(int rows) { return rollout_set_rows_big(rows); }
 
 DOPINF_API int dopinf_tune_rollout_rows(int rows) { return rollout_set_rows(rows); }
 

@@ -1,22 +1,12 @@
 // Rollouts of learned quadratic ROMs (Section 3.5): the discrete map of
 // eq. ROM_quad_time_discrete, or classical RK4 on eq. ROM_quad_time_cont, with the training
-// error and growth criterion of Step IV fused into the time loop.  Two kernels:
-//  * rollout_cols_kernel (below, r <= 32, the path of the workloads): column-owned layout,
-//    one launch per r, FP64 or double-word FP32 arithmetic;
-//  * rollout_kernel (r > 32): the row-split layout described here.
-//
-// Row-split kernel: one thread-block cluster of C CTAs per candidate, every candidate of every r
-// in one launch.
-// CTA rank j of the cluster keeps rows [j*rc, (j+1)*rc) of the operator O = [A | H | c]
-// (rc = ceil(r / C)) row-major in its shared memory.  Each right-hand-side evaluation builds
-// phi = [q, (q_i q_j)_{i<=j}, 1] locally (the state is replicated), forms its rows of O phi
-// with one warp per row, and stores them into the shared memory of every CTA of the cluster
-// (distributed shared memory); a hardware cluster barrier then makes the full vector visible
-// everywhere.  The stage results are double-buffered by step parity, so a CTA that runs ahead
-// never overwrites values a slower peer is still reading.  The RK4 combination, the metrics
-// and the early-exit decision are computed identically in every CTA, so the cluster stays in
-// lockstep without further communication.  FP64 throughput per SM is small on GB300, so each
-// stage state is formed once (r values) before its feature build rather than inside it.
+// error and growth criterion of Step IV fused into the time loop.  One thread-block cluster
+// per candidate, one launch per r (largest first), later launches chained by programmatic
+// dependent launch so that they run side by side.  Two layouts of the same computation:
+//  * rollout_cols_kernel (r <= 32): the operator in registers, 128 threads per CTA;
+//  * rollout_big_kernel (32 < r <= 92): the operator rows in shared memory, 256 threads.
+// Both in FP64 or in double-word FP32 arithmetic (with an FP64 pass over what the
+// double-word pass hands back).
 #include "common.cuh"
 #include <cooperative_groups.h>
 #include <math.h>
@@ -24,257 +14,13 @@
 #include <map>
 #include <type_traits>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 namespace cg = cooperative_groups;
 
 namespace dopinf {
 namespace {
-
-constexpr int RB = 256;  // threads per CTA
-constexpr int NW = RB / 32;
-
-struct SmemLayout {
-  size_t o, q, xs, kb, phi, mu, pi, pj, total;
-};
-
-// Shared layout for a CTA holding rc operator rows of width d_max, vectors of r_max.
-__host__ __device__ inline SmemLayout smem_layout(int rc, int r_max, int d_max) {
-  SmemLayout L;
-  size_t off = 0;
-  L.o = off;
-  off += (size_t)rc * d_max * sizeof(double);
-  L.q = off;
-  off += (size_t)r_max * sizeof(double);
-  L.xs = off;
-  off += (size_t)r_max * sizeof(double);
-  L.kb = off;  // [2 step parities][4 stages][r_max]
-  off += (size_t)8 * r_max * sizeof(double);
-  L.phi = off;
-  off += (size_t)d_max * sizeof(double);
-  L.mu = off;
-  off += (size_t)r_max * sizeof(double);
-  const int s_max = d_max - r_max - 1 > 0 ? d_max - r_max - 1 : 1;
-  L.pi = off;
-  off += (size_t)s_max * sizeof(unsigned short);
-  L.pj = off;
-  off += (size_t)s_max * sizeof(unsigned short);
-  L.total = (off + 15) / 16 * 16;
-  return L;
-}
-
-// Rows [i0, i1) of O phi, stored into buffer `dst` of every CTA of the cluster.
-__device__ __forceinline__ void eval_rows(cg::cluster_group& cl, const double* Os, int i0, int i1, int d,
-                                          const double* phi, double* dst) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = (int)cl.num_blocks();
-  for (int i = i0 + w; i < i1; i += NW) {
-    const double* row = Os + (size_t)(i - i0) * d;
-    double acc = 0.0;
-    for (int a = lane; a < d; a += 32) acc = fma(row[a], phi[a], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane < C) {
-      double* remote = cl.map_shared_rank(dst, (unsigned)lane);
-      remote[i] = acc;
-    }
-  }
-}
-
-__device__ __forceinline__ void build_phi(const double* x, int r, int d, const unsigned short* pi,
-                                          const unsigned short* pj, double* phi) {
-  const int s = d - r - 1;
-  for (int a = threadIdx.x; a < d; a += RB) {
-    double v;
-    if (a < r)
-      v = x[a];
-    else if (a < r + s)
-      v = x[pi[a - r]] * x[pj[a - r]];
-    else
-      v = 1.0;
-    phi[a] = v;
-  }
-}
-
-__global__ void __launch_bounds__(RB, 5) rollout_kernel(RolloutBatch bt) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cg::cluster_group cl = cg::this_cluster();
-  const int C = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const int cid = blockIdx.x / C;
-  const RolloutCand cd = bt.cands ? bt.cands[cid] : bt.one;
-  const int r = cd.r, d = cd.d;
-  const int rc = (r + C - 1) / C;
-  const int i0 = rank * rc < r ? rank * rc : r;
-  const int i1 = i0 + rc < r ? i0 + rc : r;
-  const SmemLayout L = smem_layout(bt.rc_max, bt.r_max, bt.d_max);
-  double* Os = reinterpret_cast<double*>(smraw + L.o);
-  double* q = reinterpret_cast<double*>(smraw + L.q);
-  double* xs = reinterpret_cast<double*>(smraw + L.xs);
-  double* kb = reinterpret_cast<double*>(smraw + L.kb);
-  double* phi = reinterpret_cast<double*>(smraw + L.phi);
-  double* mu = reinterpret_cast<double*>(smraw + L.mu);
-  unsigned short* pi = reinterpret_cast<unsigned short*>(smraw + L.pi);
-  unsigned short* pj = reinterpret_cast<unsigned short*>(smraw + L.pj);
-  __shared__ int s_stop;
-
-  // a failed factorisation (the same for every CTA of the cluster): nothing to roll out
-  if (bt.metrics && bt.status[cd.cand] != 0) {
-    if (rank == 0 && threadIdx.x == 0) {
-      bt.train_err[cd.cand] = INFINITY;
-      bt.growth[cd.cand] = INFINITY;
-      if (bt.steps) bt.steps[cd.cand] = 0;
-    }
-    return;
-  }
-  for (int64_t e = threadIdx.x; e < (int64_t)(i1 - i0) * d; e += RB) {
-    const int i = i0 + (int)(e / d), a = (int)(e % d);
-    Os[e] = cd.O[i + (size_t)a * cd.ldo];
-  }
-  for (int i = threadIdx.x; i < r; i += RB) {
-    const int off = i * r - i * (i - 1) / 2;  // column r + off(i) + (j - i) multiplies x_i x_j
-    for (int j = i; j < r; ++j) {
-      pi[off + j - i] = (unsigned short)i;
-      pj[off + j - i] = (unsigned short)j;
-    }
-  }
-  for (int i = threadIdx.x; i < r; i += RB) {
-    q[i] = bt.q0[i];
-    mu[i] = bt.metrics ? cd.mu[i] : 0.0;
-  }
-  if (threadIdx.x == 0) s_stop = 0;
-  cl.sync();  // every CTA initialised before any remote store
-
-  const double dt = bt.dt, h2 = 0.5 * dt, h6 = dt / 6.0;
-  const double denom = bt.metrics ? *cd.denom : 1.0;
-  // max over t < k of num/den (the training error is its square root: sqrt is monotone and
-  // correctly rounded, so this is the maximum of the square roots), and the bits of the
-  // largest |q - mu| (non-negative doubles order like their bit patterns)
-  double rat = 0.0;
-  unsigned long long gnumb = 0ull;
-  // growth >= max_growth, decided without a division outside a band of 2^-40 around the
-  // threshold (the division and the product each round by 2^-53)
-  const double thr = bt.max_growth * denom;
-  const bool band_ok = denom > 0.0 && isfinite(thr) && thr > 0.0;
-  const unsigned long long band_lo =
-      band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 - 0x1p-40)) : 0ull;
-  const unsigned long long band_hi =
-      band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + 0x1p-40)) : ~0ull;
-  int st = 0;
-  int64_t t_end = 0;  // the last state whose metrics were formed (= steps advanced)
-  for (int64_t t = 0;; ++t) {
-    t_end = t;
-    // ---- metrics and output of state t (warp 0 of every CTA, identical results) ----
-    // They sit in front of the step's first evaluation, so they avoid the FP64 pipe where the
-    // result does not change: max |q - mu| as an integer maximum of the (non-negative) bit
-    // patterns, the training error as the maximum of num/den with one square root at the end,
-    // and the growth test against a band around max_growth * denom (the division only inside).
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      bool fin = true;
-      unsigned long long devb = 0ull;
-      double num = 0.0, den = 0.0;
-      for (int i = lane; i < r; i += 32) {
-        const double v = q[i];
-        fin = fin && isfinite(v);
-        if (bt.metrics) {
-          const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v - mu[i]));
-          devb = b > devb ? b : devb;
-          if (t < bt.k) {
-            const double h = bt.Qhat[i + t * bt.ldqh];
-            num += (v - h) * (v - h);
-            den += h * h;
-          }
-        }
-        if (bt.traj && rank == 0) bt.traj_out[t * r + i] = v;
-      }
-      fin = __all_sync(0xffffffffu, fin);
-      if (bt.metrics) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long ob = __shfl_xor_sync(0xffffffffu, devb, o);
-          devb = ob > devb ? ob : devb;
-          if (t < bt.k) {
-            num += __shfl_xor_sync(0xffffffffu, num, o);
-            den += __shfl_xor_sync(0xffffffffu, den, o);
-          }
-        }
-        if (fin) {
-          gnumb = devb > gnumb ? devb : gnumb;
-          if (t < bt.k) rat = fmax(rat, num / den);
-        }
-      }
-      if (lane == 0) {
-        int stop = 0;
-        if (!fin) {
-          st = 2;
-          stop = 1;
-        } else if (bt.metrics && gnumb >= band_lo &&
-                   (gnumb > band_hi || __longlong_as_double((long long)gnumb) / denom >= bt.max_growth)) {
-          st = 3;
-          stop = 1;
-        }
-        if (t + 1 >= bt.n_steps) stop = 1;
-        s_stop = stop;
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    double* kp = kb + (size_t)(t & 1) * 4 * bt.r_max;  // this step's stage buffers
-    double* k1 = kp;
-    double* k2 = kp + bt.r_max;
-    double* k3 = kp + 2 * bt.r_max;
-    double* k4 = kp + 3 * bt.r_max;
-    if (bt.mode == DOPINF_DISCRETE) {
-      build_phi(q, r, d, pi, pj, phi);
-      __syncthreads();
-      eval_rows(cl, Os, i0, i1, d, phi, k1);
-      cl.sync();
-      for (int i = threadIdx.x; i < r; i += RB) q[i] = k1[i];
-    } else {
-      // products and sums rounded separately, in the order q + (dt/6)(((k1 + 2 k2) + 2 k3) + k4)
-      build_phi(q, r, d, pi, pj, phi);
-      __syncthreads();
-      eval_rows(cl, Os, i0, i1, d, phi, k1);
-      cl.sync();
-      for (int i = threadIdx.x; i < r; i += RB) xs[i] = __dadd_rn(q[i], __dmul_rn(h2, k1[i]));
-      __syncthreads();
-      build_phi(xs, r, d, pi, pj, phi);
-      __syncthreads();
-      eval_rows(cl, Os, i0, i1, d, phi, k2);
-      cl.sync();
-      for (int i = threadIdx.x; i < r; i += RB) xs[i] = __dadd_rn(q[i], __dmul_rn(h2, k2[i]));
-      __syncthreads();
-      build_phi(xs, r, d, pi, pj, phi);
-      __syncthreads();
-      eval_rows(cl, Os, i0, i1, d, phi, k3);
-      cl.sync();
-      for (int i = threadIdx.x; i < r; i += RB) xs[i] = __dadd_rn(q[i], __dmul_rn(dt, k3[i]));
-      __syncthreads();
-      build_phi(xs, r, d, pi, pj, phi);
-      __syncthreads();
-      eval_rows(cl, Os, i0, i1, d, phi, k4);
-      cl.sync();
-      for (int i = threadIdx.x; i < r; i += RB) {
-        const double sum = __dadd_rn(__dadd_rn(__dadd_rn(k1[i], 2.0 * k2[i]), 2.0 * k3[i]), k4[i]);
-        q[i] = __dadd_rn(q[i], __dmul_rn(h6, sum));
-      }
-    }
-    __syncthreads();
-  }
-  cl.sync();  // no CTA leaves while a peer may still store into its shared memory
-  if (rank == 0 && threadIdx.x == 0) {
-    if (bt.steps) bt.steps[cd.cand] = t_end;
-    if (bt.metrics) {
-      bt.status[cd.cand] = st;
-      bt.train_err[cd.cand] = st == 0 ? sqrt(rat) : INFINITY;
-      bt.growth[cd.cand] = st == 2 ? INFINITY : __longlong_as_double((long long)gnumb) / denom;
-    }
-    if (bt.traj && bt.finite) *bt.finite = st == 2 ? 0 : 1;
-  }
-}
-
-constexpr size_t kRolloutSmemMax = 200 * 1024;
 
 // ---------------------------------------------------------------------------------------
 // Column-owned rollouts for r <= 32.  FP64 issue on GB300 is one warp instruction per 64
@@ -363,7 +109,8 @@ __device__ __forceinline__ csum shfl_x(csum v, int o) {
 __device__ __forceinline__ double add_v(double a, double b) { return a + b; }
 __device__ __forceinline__ csum add_v(csum a, csum b) { return csum_add(a, b); }
 
-// Warp sum of each of the RC values per lane; lane L returns the sum of row L >> (5 - log2 RC).
+// Warp sum of each of the RC values per lane (RC = 1, 2, 4, 8); lane L returns the sum of row
+// L >> (5 - log2 RC).
 // At each level a lane keeps half of its values and adds the half its partner sends, so the
 // tree of every row is the full butterfly over the 32 lanes (the same for every RC); partners
 // form identical sums because both additions are commutative.
@@ -375,16 +122,26 @@ __device__ __forceinline__ V warp_rows_sum(const V (&acc)[RC], int lane) {
   } else if constexpr (RC == 2) {
     const bool up = lane & 16;
     k = add_v(up ? acc[1] : acc[0], shfl_x(up ? acc[0] : acc[1], 16));
-  } else {
-    static_assert(RC == 4, "RC is 1, 2 or 4");
+  } else if constexpr (RC == 4) {
     const bool up = lane & 16;
     const V k0 = add_v(up ? acc[2] : acc[0], shfl_x(up ? acc[0] : acc[2], 16));
     const V k1 = add_v(up ? acc[3] : acc[1], shfl_x(up ? acc[1] : acc[3], 16));
     const bool up8 = lane & 8;
     k = add_v(up8 ? k1 : k0, shfl_x(up8 ? k0 : k1, 8));
+  } else {
+    static_assert(RC == 8, "RC is 1, 2, 4 or 8");
+    const bool up = lane & 16;
+    V h[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) h[m] = add_v(up ? acc[4 + m] : acc[m], shfl_x(up ? acc[m] : acc[4 + m], 16));
+    const bool up8 = lane & 8;
+    const V j0 = add_v(up8 ? h[2] : h[0], shfl_x(up8 ? h[0] : h[2], 8));
+    const V j1 = add_v(up8 ? h[3] : h[1], shfl_x(up8 ? h[1] : h[3], 8));
+    const bool up4 = lane & 4;
+    k = add_v(up4 ? j1 : j0, shfl_x(up4 ? j0 : j1, 4));
   }
 #pragma unroll
-  for (int o = (RC == 4 ? 4 : 8); o > 0; o >>= 1) k = add_v(k, shfl_x(k, o));
+  for (int o = (RC == 8 ? 2 : RC == 4 ? 4 : 8); o > 0; o >>= 1) k = add_v(k, shfl_x(k, o));
   return k;
 }
 
@@ -495,16 +252,21 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
     const dw dtw = dw_of(dt), h2w = dw_of(h2), h6w = dw_of(h6);
     const double denom = bt.metrics ? *cd.denom : 1.0;
     // metrics as in the row-split kernel: max of num/den (one square root at the end), the
-    // largest |q - mu| as an integer maximum of bit patterns, growth decided by a band of
-    // 2^-40 around max_growth * denom with the division only inside it
+    // largest |q - mu| as an integer maximum of bit patterns.  FP64: growth decided by a band
+    // of 2^-40 around max_growth * denom with the division only inside it.  Double-word: the
+    // state differs from the FP64 one by rounding, so a growth inside a band of 2^-20 around
+    // the threshold hands the candidate to the FP64 kernel instead of deciding it here; since
+    // the growth maximum only rises, a candidate stopped for growth above the band stops at
+    // the same step in FP64, and a valid one stays below the threshold there too.
     double rat = 0.0;
     unsigned long long gnumb = 0ull;
     const double thr = bt.max_growth * denom;
     const bool band_ok = denom > 0.0 && isfinite(thr) && thr > 0.0;
+    const double bw = DW ? 0x1p-20 : 0x1p-40;
     const unsigned long long band_lo =
-        band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 - 0x1p-40)) : 0ull;
+        band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 - bw)) : 0ull;
     const unsigned long long band_hi =
-        band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + 0x1p-40)) : ~0ull;
+        band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + bw)) : ~0ull;
     int st = 0;
 
     // metrics of state t (warp 0); lane 0 publishes the stop decision
@@ -544,10 +306,14 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
         if (!fin) {
           st = DW ? kStatusRedo : 2;
           stop = 1;
-        } else if (bt.metrics && gnumb >= band_lo &&
-                   (gnumb > band_hi || __longlong_as_double((long long)gnumb) / denom >= bt.max_growth)) {
-          st = 3;
-          stop = 1;
+        } else if (bt.metrics && gnumb >= band_lo) {
+          if constexpr (DW) {
+            st = gnumb > band_hi ? 3 : kStatusRedo;
+            stop = 1;
+          } else if (gnumb > band_hi || __longlong_as_double((long long)gnumb) / denom >= bt.max_growth) {
+            st = 3;
+            stop = 1;
+          }
         }
         if (t + 1 >= bt.n_steps) stop = 1;
         s_stop = stop;
@@ -724,13 +490,14 @@ void* cols_kernel(int nt, int rc, bool dw) {
 
 int g_rows_want = 4;  // tunable: rows of O per CTA in the column-owned rollouts
 
-// Whether a cluster of c CTAs of this kernel can be resident (sizes above 8 need the
-// non-portable attribute and enough SMs in one GPC); cached per kernel and size.
-bool cluster_fits(void* fn, int c) {
+// Whether a cluster of c CTAs of this kernel (threads per CTA, dynamic shared memory) can be
+// resident (sizes above 8 need the non-portable attribute and enough SMs in one GPC); cached
+// per kernel, size and shared memory.
+bool cluster_fits(void* fn, int c, int threads = RB5, size_t smem = 0) {
   static std::mutex mu;
-  static std::map<std::pair<void*, int>, bool> cache;
+  static std::map<std::tuple<void*, int, size_t>, bool> cache;
   std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(fn, c);
+  const auto key = std::make_tuple(fn, c, smem);
   const auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   bool ok = true, refused = false;
@@ -738,10 +505,15 @@ bool cluster_fits(void* fn, int c) {
     ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     refused = !ok;
   }
+  if (ok && smem > 48 * 1024) {
+    ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    refused = refused || !ok;
+  }
   if (ok) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c, 1, 1);
-    cfg.blockDim = dim3(RB5, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)c;
@@ -760,6 +532,415 @@ bool cluster_fits(void* fn, int c) {
   cache[key] = ok;
   return ok;
 }
+
+// ---------------------------------------------------------------------------------------
+// Column-owned rollouts for 32 < r <= 92 (the batched-learn workloads reach r = 80,
+// d = 3321; at r = 92 six rows of d = 4371 fill the 227 KB of shared memory).  The operator no longer fits registers, so each CTA keeps its RC rows of O in
+// shared memory (row rho at rho * d: a warp reads 32 consecutive entries of a row, free of
+// bank conflicts), and 256 threads walk the d columns: thread tid forms phi_a for the
+// columns a = tid + 256 j from the stage state and adds O[i][a] phi_a into its RC row sums.
+//  * a transposed butterfly reduces the RC row sums of each warp (padded to 4 or 8 rows) to
+//    one sum per row; the eight warp sums of a row are added in a fixed tree by a lane of
+//    warp 1, which stores the row's value into the evaluation buffer of every CTA of the
+//    cluster (distributed shared memory) before one cluster barrier (arrive.release ...
+//    wait.acquire);
+//  * the evaluation buffers alternate by evaluation parity, so a CTA that runs ahead never
+//    writes into a buffer a slower peer is still reading;
+//  * warp 0 owns the state (lane L: entries L, L + 32, L + 64), applies the RK4 stage
+//    combination identically in every CTA and forms the metrics of state t between its
+//    arrival at the first barrier of step t and its wait there.
+// The row sums are the same trees over the same column partial sums whatever RC and the
+// cluster size are, so the results do not depend on the launch shape.  Arithmetic: FP64, or
+// double-word with the FP64 hand-back rules of the kernel for r <= 32.
+constexpr int RBB = 256;
+constexpr int NWB = RBB / 32;
+constexpr int kMaxRB = 96;       // state entries: three per lane of warp 0
+constexpr int kMaxRBig = 92;     // largest r whose rows fit shared memory in clusters of 16
+constexpr size_t kSmemBig = 227 * 1024 - 64;  // dynamic shared memory per CTA
+constexpr int kMinRowsB = 3, kMaxRowsB = 8;
+
+struct BigLayout {
+  size_t o, pair, x, k, part, total;
+};
+
+// Shared memory of one CTA holding rc rows of an operator of width d (8 bytes per entry in
+// both arithmetics: a double, or the (high, low) binary32 pair).
+__host__ __device__ inline BigLayout big_layout(int rc, int d) {
+  BigLayout L;
+  size_t off = 0;
+  L.o = off;
+  off += (size_t)rc * d * 8;
+  L.pair = off;
+  off += ((size_t)d * 4 + 15) / 16 * 16;
+  L.x = off;  // stage state, kMaxRB + 2 entries (x[r] = 1)
+  off += (size_t)(kMaxRB + 2) * 8;
+  L.k = off;  // evaluation results by parity
+  off += (size_t)2 * kMaxRB * 8;
+  L.part = off;  // warp sums [warp][row]
+  off += (size_t)NWB * kMaxRowsB * 8;
+  L.total = (off + 15) / 16 * 16;
+  return L;
+}
+
+template <int RC, bool DW>
+__global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, int cand0) {
+  using Part = typename std::conditional<DW, csum, double>::type;
+  constexpr int RCP = RC <= 4 ? 4 : 8;  // rows of the transposed butterfly (zero-padded)
+  extern __shared__ __align__(16) unsigned char smb[];
+  __shared__ int s_stop, s_bad;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) pdl_trigger();
+  const RolloutCand cd = bt.cands ? bt.cands[cand0 + (int)(blockIdx.x / C)] : bt.one;
+  const int r = cd.r, d = cd.d, i0 = rank * RC;
+  const int nrow = r - i0 < 0 ? 0 : (r - i0 < RC ? r - i0 : RC);  // rows this CTA owns
+  const BigLayout L = big_layout(RC, d);
+  double* Os = reinterpret_cast<double*>(smb + L.o);     // FP64 operator rows
+  float2* Ow = reinterpret_cast<float2*>(smb + L.o);     // double-word operator rows
+  unsigned* pair = reinterpret_cast<unsigned*>(smb + L.pair);
+  double* xs = reinterpret_cast<double*>(smb + L.x);
+  float2* xw = reinterpret_cast<float2*>(smb + L.x);
+  double* kd = reinterpret_cast<double*>(smb + L.k);
+  float2* kw = reinterpret_cast<float2*>(smb + L.k);
+  Part* part = reinterpret_cast<Part*>(smb + L.part);
+
+  const int want = (!DW && bt.redo) ? kStatusRedo : 0;
+  bool run = !(bt.metrics && bt.status[cd.cand] != want);
+  if (!run && !bt.redo && rank == 0 && tid == 0 && bt.status[cd.cand] != kStatusRedo) {
+    bt.train_err[cd.cand] = INFINITY;
+    bt.growth[cd.cand] = INFINITY;
+    if (bt.steps) bt.steps[cd.cand] = 0;
+  }
+  if (!run) {
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) pdl_wait();
+    return;
+  }
+
+  // operator rows (zero rows past r), the phi index pairs, the constant entry of the state
+  bool bad = false;
+  for (int e = tid; e < RC * d; e += RBB) {
+    const int rho = e / d, a = e - rho * d, i = i0 + rho;
+    const double v = i < r ? cd.O[i + (size_t)a * cd.ldo] : 0.0;
+    if constexpr (DW) {
+      bad = bad || !(fabs(v) <= kDwRange);
+      const dw w = dw_of(v);
+      Ow[e] = make_float2(w.h, w.l);
+    } else {
+      Os[e] = v;
+    }
+  }
+  for (int i = tid; i < r; i += RBB) {
+    const int off = r + i * r - i * (i - 1) / 2;  // column of x_i x_i
+    for (int j = i; j < r; ++j) pair[off + j - i] = (unsigned)i | ((unsigned)j << 8);
+    pair[i] = (unsigned)i | ((unsigned)r << 8);  // linear term x_i * 1
+  }
+  if (tid == 0) pair[d - 1] = (unsigned)r | ((unsigned)r << 8);  // constant term 1 * 1
+  if constexpr (DW) {
+    if (warp == 0)
+      for (int j = 0; j < 3; ++j) {
+        const int i = lane + 32 * j;
+        if (i < r) bad = bad || !(fabs(bt.q0[i]) <= kDwRange);
+      }
+    const int any = __syncthreads_or(bad);
+    if (tid == 0) s_bad = any;
+  }
+  cl.sync();  // every CTA has started and published its flag before any remote access
+  if constexpr (DW) {
+    int peer = 0;
+    if (tid < C) peer = *cl.map_shared_rank(&s_bad, (unsigned)tid);
+    if (__syncthreads_or(peer)) {
+      if (rank == 0 && tid == 0) bt.status[cd.cand] = kStatusRedo;
+      cl.sync();  // every CTA has read its peers' flags before any of them leaves
+      if (blockIdx.x == gridDim.x - 1 && tid == 0) pdl_wait();
+      return;
+    }
+  }
+
+  // state: warp 0, lane L owns entries L, L + 32, L + 64
+  double qv[3], mu[3], hcur[3];
+  dw qw[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int i = lane + 32 * j;
+    const bool own = warp == 0 && i < r;
+    qv[j] = own ? bt.q0[i] : 0.0;
+    qw[j] = dw_of(qv[j]);
+    mu[j] = (own && bt.metrics) ? cd.mu[i] : 0.0;
+    hcur[j] = (own && bt.metrics && bt.k > 0) ? bt.Qhat[i] : 0.0;
+    if (own) {
+      if constexpr (DW)
+        xw[i] = make_float2(qw[j].h, qw[j].l);
+      else
+        xs[i] = qv[j];
+    }
+  }
+  if (tid == 0) {
+    if constexpr (DW)
+      xw[r] = make_float2(1.0f, 0.0f);
+    else
+      xs[r] = 1.0;
+  }
+  const double dt = bt.dt, h2 = 0.5 * dt, h6 = dt / 6.0;
+  const dw dtw = dw_of(dt), h2w = dw_of(h2), h6w = dw_of(h6);
+  const double denom = bt.metrics ? *cd.denom : 1.0;
+  double rat = 0.0;
+  unsigned long long gnumb = 0ull;
+  const double thr = bt.max_growth * denom;
+  const bool band_ok = denom > 0.0 && isfinite(thr) && thr > 0.0;
+  const double bw = DW ? 0x1p-20 : 0x1p-40;
+  const unsigned long long band_lo = band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 - bw)) : 0ull;
+  const unsigned long long band_hi = band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + bw)) : ~0ull;
+  int st = 0;
+
+  // metrics of state t (warp 0, the same values in every CTA); lane 0 publishes the decision
+  auto check = [&](int64_t t) {
+    bool fin = true;
+    unsigned long long devb = 0ull;
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int i = lane + 32 * j;
+      if (i >= r) continue;
+      if constexpr (DW) qv[j] = dw_value(qw[j]);
+      fin = fin && isfinite(qv[j]);
+      if (bt.metrics) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(qv[j] - mu[j]));
+        devb = b > devb ? b : devb;
+        if (t < bt.k) {
+          num += (qv[j] - hcur[j]) * (qv[j] - hcur[j]);
+          den += hcur[j] * hcur[j];
+        }
+      }
+      if (bt.traj && rank == 0) bt.traj_out[t * r + i] = qv[j];
+    }
+    fin = __all_sync(kFull, fin);
+    if (bt.metrics) {
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kFull, devb, o2);
+        devb = ob > devb ? ob : devb;
+      }
+      if (t < bt.k) {
+        const double nd[2] = {num, den};
+        const double v = warp_rows_sum<2>(nd, lane);  // lanes < 16: num, lanes >= 16: den
+        num = v;
+        den = __shfl_sync(kFull, v, 16);
+      }
+      if (lane == 0 && fin) {
+        gnumb = devb > gnumb ? devb : gnumb;
+        if (t < bt.k) rat = fmax(rat, num / den);
+      }
+    }
+    if (lane == 0) {
+      int stop = 0;
+      if (!fin) {
+        st = DW ? kStatusRedo : 2;
+        stop = 1;
+      } else if (bt.metrics && gnumb >= band_lo) {
+        if constexpr (DW) {
+          st = gnumb > band_hi ? 3 : kStatusRedo;
+          stop = 1;
+        } else if (gnumb > band_hi || __longlong_as_double((long long)gnumb) / denom >= bt.max_growth) {
+          st = 3;
+          stop = 1;
+        }
+      }
+      if (t + 1 >= bt.n_steps) stop = 1;
+      s_stop = stop;
+    }
+  };
+
+  // one right-hand-side evaluation at the stage state; the r results land in this CTA's
+  // evaluation buffer of parity e & 1 (and in every peer's)
+  unsigned e = 0;
+  auto eval = [&](bool with_check, int64_t t) {
+    Part acc[RCP];
+#pragma unroll
+    for (int rho = 0; rho < RCP; ++rho) acc[rho] = Part{};
+    for (int a = tid; a < d; a += RBB) {
+      const unsigned p = pair[a];
+      const int ia = (int)(p & 0xffu), ib = (int)(p >> 8);
+      if constexpr (DW) {
+        const float2 xa = xw[ia], xb = xw[ib];
+        const float ph = __fmul_rn(xa.x, xb.x);
+        const float pl = __fmaf_rn(xa.y, xb.x, __fmaf_rn(xa.x, xb.y, __fmaf_rn(xa.x, xb.x, -ph)));
+#pragma unroll
+        for (int rho = 0; rho < RC; ++rho) {
+          const float2 ov = Ow[rho * d + a];
+          const float pr = __fmul_rn(ov.x, ph);
+          const float err = __fmaf_rn(ov.y, ph, __fmaf_rn(ov.x, pl, __fmaf_rn(ov.x, ph, -pr)));
+          const dw u = two_sum(acc[rho].s, pr);
+          acc[rho].s = u.h;
+          acc[rho].c = __fadd_rn(acc[rho].c, __fadd_rn(u.l, err));
+        }
+      } else {
+        const double ph = xs[ia] * xs[ib];
+#pragma unroll
+        for (int rho = 0; rho < RC; ++rho) acc[rho] = fma(Os[rho * d + a], ph, acc[rho]);
+      }
+    }
+    const Part v = warp_rows_sum<RCP>(acc, lane);
+    constexpr int per = 32 / RCP;  // lanes holding each row's sum
+    if ((lane & (per - 1)) == 0 && lane / per < RC) part[warp * kMaxRowsB + lane / per] = v;
+    __syncthreads();
+    const int buf = (int)(e & 1u);
+    if (warp == 1 && lane < nrow) {
+      const Part* pp = part + lane;
+      const Part s = add_v(add_v(add_v(pp[0 * kMaxRowsB], pp[1 * kMaxRowsB]), add_v(pp[2 * kMaxRowsB], pp[3 * kMaxRowsB])),
+                           add_v(add_v(pp[4 * kMaxRowsB], pp[5 * kMaxRowsB]), add_v(pp[6 * kMaxRowsB], pp[7 * kMaxRowsB])));
+      const int i = i0 + lane;
+      if constexpr (DW) {
+        const dw s2 = two_sum(s.s, s.c);
+        const float2 val = make_float2(s2.h, s2.l);
+        for (int j = 0; j < C; ++j) cl.map_shared_rank(kw + buf * kMaxRB, (unsigned)j)[i] = val;
+      } else {
+        for (int j = 0; j < C; ++j) cl.map_shared_rank(kd + buf * kMaxRB, (unsigned)j)[i] = s;
+      }
+    }
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    if (with_check && warp == 0) {
+      check(t);
+      __syncwarp();
+    }
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    ++e;
+    return buf;
+  };
+
+  __syncthreads();
+  int64_t t_end = 0;
+  double k1d[3], k2d[3], k3d[3];
+  dw k1w[3], k2w[3], k3w[3];
+  for (int64_t t = 0;; ++t) {
+    t_end = t;
+    double hnext[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int i = lane + 32 * j;
+      hnext[j] = (warp == 0 && i < r && bt.metrics && t + 1 < bt.k) ? bt.Qhat[i + (t + 1) * bt.ldqh] : 0.0;
+    }
+    int b = eval(true, t);
+    if (bt.mode == DOPINF_DISCRETE) {
+      if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int i = lane + 32 * j;
+          if (i >= r) continue;
+          if constexpr (DW) {
+            const float2 kv = kw[b * kMaxRB + i];
+            k1w[j] = dw{kv.x, kv.y};
+            xw[i] = kv;
+          } else {
+            k1d[j] = kd[b * kMaxRB + i];
+            xs[i] = k1d[j];
+          }
+        }
+      }
+      __syncthreads();
+      if (s_stop) break;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if constexpr (DW)
+          qw[j] = k1w[j];
+        else
+          qv[j] = k1d[j];
+      }
+    } else {
+      // RK4: stage s reads its evaluation, forms the next stage state (products and sums
+      // rounded separately, q + (dt/6)(((k1 + 2 k2) + 2 k3) + k4) at the end)
+      for (int s = 0; s < 4; ++s) {
+        if (s > 0) b = eval(false, t);
+        if (warp == 0) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int i = lane + 32 * j;
+            if (i >= r) continue;
+            if constexpr (DW) {
+              const float2 kv = kw[b * kMaxRB + i];
+              const dw kk{kv.x, kv.y};
+              dw x;
+              if (s == 0) {
+                k1w[j] = kk;
+                x = dw_add(qw[j], dw_mul(h2w, kk));
+              } else if (s == 1) {
+                k2w[j] = kk;
+                x = dw_add(qw[j], dw_mul(h2w, kk));
+              } else if (s == 2) {
+                k3w[j] = kk;
+                x = dw_add(qw[j], dw_mul(dtw, kk));
+              } else {
+                const dw sum = dw_add(dw_add(dw_add(k1w[j], dw_twice(k2w[j])), dw_twice(k3w[j])), kk);
+                qw[j] = dw_add(qw[j], dw_mul(h6w, sum));
+                x = qw[j];
+              }
+              xw[i] = make_float2(x.h, x.l);
+            } else {
+              const double kk = kd[b * kMaxRB + i];
+              double x;
+              if (s == 0) {
+                k1d[j] = kk;
+                x = __dadd_rn(qv[j], __dmul_rn(h2, kk));
+              } else if (s == 1) {
+                k2d[j] = kk;
+                x = __dadd_rn(qv[j], __dmul_rn(h2, kk));
+              } else if (s == 2) {
+                k3d[j] = kk;
+                x = __dadd_rn(qv[j], __dmul_rn(dt, kk));
+              } else {
+                const double sum = __dadd_rn(__dadd_rn(__dadd_rn(k1d[j], 2.0 * k2d[j]), 2.0 * k3d[j]), kk);
+                qv[j] = __dadd_rn(qv[j], __dmul_rn(h6, sum));
+                x = qv[j];
+              }
+              xs[i] = x;
+            }
+          }
+        }
+        __syncthreads();
+        if (s == 0 && s_stop) break;
+      }
+      if (s_stop) break;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) hcur[j] = hnext[j];
+  }
+  cl.sync();  // no CTA leaves while a peer may still store into its shared memory
+  if (rank == 0 && tid == 0) {
+    if (DW && st == kStatusRedo) {
+      bt.status[cd.cand] = kStatusRedo;
+    } else {
+      if (bt.steps) bt.steps[cd.cand] = t_end;
+      if (bt.metrics) {
+        bt.status[cd.cand] = st;
+        bt.train_err[cd.cand] = st == 0 ? sqrt(rat) : INFINITY;
+        bt.growth[cd.cand] = st == 2 ? INFINITY : __longlong_as_double((long long)gnumb) / denom;
+      }
+      if (bt.traj && bt.finite) *bt.finite = st == 2 ? 0 : 1;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && tid == 0) pdl_wait();
+}
+
+template <int RC, bool DW>
+void* big_kernel_ptr() {
+  return reinterpret_cast<void*>(&rollout_big_kernel<RC, DW>);
+}
+
+void* big_kernel(int rc, bool dw) {
+  using F = void* (*)();
+  static const F tab[2][kMaxRowsB - kMinRowsB + 1] = {
+      {big_kernel_ptr<3, false>, big_kernel_ptr<4, false>, big_kernel_ptr<5, false>, big_kernel_ptr<6, false>,
+       big_kernel_ptr<7, false>, big_kernel_ptr<8, false>},
+      {big_kernel_ptr<3, true>, big_kernel_ptr<4, true>, big_kernel_ptr<5, true>, big_kernel_ptr<6, true>,
+       big_kernel_ptr<7, true>, big_kernel_ptr<8, true>},
+  };
+  if (rc < kMinRowsB || rc > kMaxRowsB) return nullptr;
+  return tab[dw ? 1 : 0][rc - kMinRowsB]();
+}
+
+int g_rows_big_want = 4;  // tunable: rows of O per CTA for r > 32
 
 }  // namespace
 
@@ -825,40 +1006,81 @@ int launch_rollouts_cols(RolloutBatch bt, int cand0, int n, int r, bool chained,
   return launch_status();
 }
 
-size_t rollout_smem_bytes(int cluster, int r_max, int d_max) {
-  return smem_layout((r_max + cluster - 1) / cluster, r_max, d_max).total;
+bool rollout_big_supported(int r) { return r > kMaxR5 && r <= kMaxRBig; }
+
+// Rows per CTA, cluster size and shared memory of the kernel for 32 < r <= 92 (0 if none
+// fits): the preferred rows, raised until the cluster has at most 16 CTAs and both
+// arithmetics' kernels can be resident.
+int rollout_big_shape(int r, int* rows, int* cluster, size_t* smem) {
+  if (!rollout_big_supported(r)) return 0;
+  const int d = dim_d(r);
+  int rc = g_rows_big_want;
+  if (rc * 16 < r) rc = (r + 15) / 16;
+  for (; rc <= kMaxRowsB; ++rc) {
+    const int c = (r + rc - 1) / rc;
+    const size_t sm = big_layout(rc, d).total;
+    if (sm > kSmemBig) break;
+    void* f64 = big_kernel(rc, false);
+    void* fdw = big_kernel(rc, true);
+    if (f64 && fdw && cluster_fits(f64, c, RBB, sm) && cluster_fits(fdw, c, RBB, sm)) {
+      *rows = rc;
+      *cluster = c;
+      *smem = sm;
+      return 1;
+    }
+  }
+  return 0;
 }
 
-int rollout_cluster_size(int r_max, int d_max, int want) {
-  int c = 1;
-  while (c < want && c < 8) c *= 2;
-  while (c < 8 && rollout_smem_bytes(c, r_max, d_max) > kRolloutSmemMax) c *= 2;
-  return rollout_smem_bytes(c, r_max, d_max) <= kRolloutSmemMax ? c : 0;
+int rollout_set_rows_big(int rc) {
+  const int prev = g_rows_big_want;
+  if (rc >= kMinRowsB && rc <= kMaxRowsB) g_rows_big_want = rc;
+  return prev;
 }
 
-int launch_rollouts(RolloutBatch bt, int cluster, cudaStream_t st) {
-  if (cluster < 1 || cluster > 8 || bt.n_cand < 1) return DOPINF_E_ARG;
-  bt.rc_max = (bt.r_max + cluster - 1) / cluster;
-  const size_t smem = rollout_smem_bytes(cluster, bt.r_max, bt.d_max);
-  if (smem > kRolloutSmemMax) return DOPINF_E_UNSUPPORTED;
-  DOPINF_CUDA(cudaFuncSetAttribute(rollout_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRolloutSmemMax));
+// Candidates [cand0, cand0 + n) of one rank r > 32; chained as launch_rollouts_cols.
+int launch_rollouts_big(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st) {
+  int rc = 0, c = 0;
+  size_t smem = 0;
+  if (n < 1 || !rollout_big_shape(r, &rc, &c, &smem)) return DOPINF_E_UNSUPPORTED;
+  void* fn = big_kernel(rc, bt.arith == DOPINF_ROLLOUT_DW);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(bt.n_cand * cluster), 1, 1);
-  cfg.blockDim = dim3(RB, 1, 1);
+  cfg.gridDim = dim3((unsigned)(n * c), 1, 1);
+  cfg.blockDim = dim3(RBB, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.x = (unsigned)c;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  DOPINF_CUDA(cudaLaunchKernelEx(&cfg, rollout_kernel, bt));
+  cfg.numAttrs = chained ? 2 : 1;
+  void* args[] = {&bt, &cand0};
+  DOPINF_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
   return launch_status();
 }
 
+bool rollout_supported(int r) { return rollout_cols_supported(r) || rollout_big_supported(r); }
+
+// Shape of the launch for rank r with either kernel (0 if none fits).
+int rollout_shape(int r) {
+  int rc = 0, c = 0;
+  size_t sm = 0;
+  return r <= kMaxR5 ? rollout_cols_shape(r, &rc, &c) : rollout_big_shape(r, &rc, &c, &sm);
+}
+
+int launch_rollouts_rank(RolloutBatch bt, int cand0, int n, int r, bool chained, cudaStream_t st) {
+  return r <= kMaxR5 ? launch_rollouts_cols(bt, cand0, n, r, chained, st)
+                     : launch_rollouts_big(bt, cand0, n, r, chained, st);
+}
+
 }  // namespace dopinf
+
+using namespace dopinf;
+
 
 using namespace dopinf;
 
@@ -866,11 +1088,8 @@ DOPINF_API int dopinf_rollout(const double* O, int r, int64_t ldo, const double*
                               double dt, double* Qtilde, int* finite, void* stream) {
   if (!O || !q0 || !Qtilde || r < 1 || r > 255 || ldo < r || n_steps < 1) return DOPINF_E_ARG;
   if (mode != DOPINF_DISCRETE && mode != DOPINF_CONTINUOUS_RK4) return DOPINF_E_ARG;
+  if (!rollout_supported(r) || !rollout_shape(r)) return DOPINF_E_UNSUPPORTED;
   const int d = dim_d(r);
-  int rc = 0, c_cols = 0;
-  const bool cols = rollout_cols_shape(r, &rc, &c_cols) != 0;
-  const int cluster = cols ? 0 : rollout_cluster_size(r, d, r >= 16 ? 4 : 1);
-  if (!cols && !cluster) return DOPINF_E_UNSUPPORTED;
   RolloutBatch bt = {};
   bt.cands = nullptr;  // the single candidate travels inside the launch arguments
   bt.one.O = O;
@@ -889,6 +1108,5 @@ DOPINF_API int dopinf_rollout(const double* O, int r, int64_t ldo, const double*
   bt.traj_out = Qtilde;
   bt.finite = finite;
   bt.arith = DOPINF_ROLLOUT_FP64;
-  if (cols) return launch_rollouts_cols(bt, 0, 1, r, false, as_stream(stream));
-  return launch_rollouts(bt, cluster, as_stream(stream));
+  return launch_rollouts_rank(bt, 0, 1, r, false, as_stream(stream));
 }

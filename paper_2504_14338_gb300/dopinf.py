@@ -75,8 +75,10 @@ def _load():
                                         ctypes.c_double, _c_i64, ctypes.c_double, _c_p, _c_p, _c_p, _c_p,
                                         ctypes.POINTER(ctypes.c_int), _c_p, ctypes.POINTER(ctypes.c_double), _c_p,
                                         _c_sz, _c_p]),
+        "dopinf_learn_operator_offset": (_c_sz, [_c_i64, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
-        "dopinf_tune_learn_cluster": (ctypes.c_int, [ctypes.c_int]),
+        "dopinf_tune_rollout_rows_large": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_arith": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_reduce_coop": (ctypes.c_int, [ctypes.c_int]),
@@ -212,15 +214,15 @@ def dopinf_tune_gram_chunk(rows=0):
     return int(lib.dopinf_tune_gram_chunk(int(rows)))
 
 
-def dopinf_tune_learn_cluster(cluster=0):
-    """Sets (1, 2, 4, 8) or queries the cluster size of the row-split rollouts (used when an r
-    of the list is above 32); returns the previous value."""
-    return int(lib.dopinf_tune_learn_cluster(int(cluster)))
+def dopinf_tune_rollout_rows_large(rows=0):
+    """Sets (3 to 8) or queries the operator rows per CTA of the rollouts of 32 < r <= 92 (the
+    cluster of one candidate has ceil(r / rows) CTAs, at most 16); returns the previous value."""
+    return int(lib.dopinf_tune_rollout_rows_large(int(rows)))
 
 
 def dopinf_tune_rollout_arith(arith=0):
-    """Sets (ROLLOUT_FP64, ROLLOUT_DW) or queries the arithmetic of the learn rollouts of r <= 32;
-    returns the previous value."""
+    """Sets (ROLLOUT_FP64, ROLLOUT_DW) or queries the arithmetic of the learn rollouts; returns
+    the previous value."""
     return int(lib.dopinf_tune_rollout_arith(int(arith)))
 
 
@@ -293,8 +295,10 @@ def dopinf_learn_async(Qhat, r_list, beta1, beta2, n_steps, out, mode=DISCRETE, 
 
 
 def dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=DISCRETE, dt=1.0, max_growth=1.2, ws=None,
-                 stream=None, allow_no_stable=True):
-    """Step IV grid search.  Qhat: (r_max, k) column-major.  Returns a dict of results."""
+                 stream=None, allow_no_stable=True, operators=False):
+    """Step IV grid search.  Qhat: (r_max, k) column-major.  Returns a dict of results; with
+    operators=True also "operators": every candidate's (r, d) operator [A | H | c] copied out of
+    the workspace (None where its Cholesky factorisation failed)."""
     r_max, k = Qhat.shape
     if Qhat.stride(0) != 1:
         raise ValueError("Qhat must be column-major (r_max, k)")
@@ -320,6 +324,20 @@ def dopinf_learn(Qhat, r_list, beta1, beta2, n_steps, mode=DISCRETE, dt=1.0, max
     _check("dopinf_learn", st, (OK, E_NO_STABLE) if allow_no_stable else (OK,))
     out = dict(train_err=err, growth=gro, status=cst, steps=steps, best=best.value, O_best=O_best, code=st,
                stage_ms=dict(normal_equations=stage[0], solves=stage[1], rollouts=stage[2]))
+    if operators:
+        stat = cst.cpu().tolist()
+        nb12 = len(beta1) * len(beta2)
+        ops = []
+        for c in range(n_cand):
+            r = int(r_list[c // nb12])
+            d = r + r * (r + 1) // 2 + 1
+            off = lib.dopinf_learn_operator_offset(k, rl, len(r_list), len(beta1), len(beta2), c)
+            if stat[c] == 1:
+                ops.append(None)
+                continue
+            flat = buf[off:off + 8 * r * d].view(torch.float64)
+            ops.append(flat.view(d, r).t().clone())      # column-major r x d
+        out["operators"] = ops
     if best.value >= 0:
         nb12 = len(beta1) * len(beta2)
         r = int(r_list[best.value // nb12])

@@ -86,7 +86,8 @@ def test_arguments_rejected_before_launch():
     for k in (2817, 5_000_000, 1 << 40):
         assert f(p8, 0, 64, k, 64, 0, p8, k, z) == dp.E_UNSUPPORTED, k
     assert f(p8, 0, 64, 100, 63, 0, p8, 100, z) == dp.E_ARG      # ldq < n
-    # rollout: r = 0, ldo < r
+    # rollout: r = 0, ldo < r; r = 93 is past the widest kernel
+    assert L.dopinf_rollout(p8, 93, 93, p8, 10, 0, 1.0, p8, p8, z) == dp.E_UNSUPPORTED
     assert L.dopinf_rollout(p8, 0, 1, p8, 10, 0, 1.0, p8, p8, z) == dp.E_ARG
     assert L.dopinf_rollout(p8, 3, 2, p8, 10, 0, 1.0, p8, p8, z) == dp.E_ARG
 

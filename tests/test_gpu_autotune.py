@@ -48,22 +48,25 @@ def test_learn_same_bits_for_every_rows_setting(setup, arith):
             assert torch.equal(res[key], ref[key]), (rc, key)
 
 
-def test_learn_same_bits_for_every_cluster_size(setup):
-    """Row-split rollouts (an r above 32 in the list): clusters of 1, 2, 4 and 8 CTAs give the
-    same bits."""
+@pytest.mark.parametrize("arith", ["fp64", "dw"])
+def test_learn_same_bits_for_every_large_rows_setting(setup, arith):
+    """Rollouts of an r above 32 (operator rows in shared memory): 3 to 8 rows per CTA (clusters
+    of 12 down to 5 CTAs at r = 34) give the same bits, in both arithmetics."""
     dp, synth, w, D, Qh = setup
     Qh34 = torch.from_numpy(_reduce34(setup)).cuda().t()
     b1 = synth.logspace(-6, 2, 3)
     b2 = synth.logspace(-6, 2, 3)
-    prev = dp.dopinf_tune_learn_cluster(0)
+    prev = dp.dopinf_tune_rollout_rows_large(0)
+    prev_a = dp.dopinf_tune_rollout_arith(dp.ROLLOUT_FP64 if arith == "fp64" else dp.ROLLOUT_DW)
     runs = {}
     try:
-        for c in (1, 2, 4, 8):
-            dp.dopinf_tune_learn_cluster(c)
+        for c in (3, 4, 5, 6, 7, 8):
+            dp.dopinf_tune_rollout_rows_large(c)
             runs[c] = dp.dopinf_learn(Qh34, [6, 34], b1, b2, 200, mode=dp.CONTINUOUS_RK4, dt=w.snap_dt)
     finally:
-        dp.dopinf_tune_learn_cluster(prev)
-    ref = runs[1]
+        dp.dopinf_tune_rollout_rows_large(prev)
+        dp.dopinf_tune_rollout_arith(prev_a)
+    ref = runs[3]
     assert (ref["status"] == 0).sum().item() >= 1
     for c, res in runs.items():
         assert res["best"] == ref["best"], c

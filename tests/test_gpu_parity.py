@@ -342,37 +342,153 @@ def arith(request, dp):
     dp.dopinf_tune_rollout_arith(prev)
 
 
+def _oracle_rollout_metrics(Op, r, Qh, n_steps, mode, dt, max_growth=1.2):
+    """The oracle's rollout of a given operator with Step IV's metrics: status (0 valid,
+    2 non-finite, 3 growth), the state index where a rollout that stops early stops (the first
+    state that is non-finite or brings the growth to max_growth), training error, growth, and
+    how far (relative) the deciding growth value lies from the threshold."""
+    Qr = np.asarray(Qh, dtype=np.float64)[:r].T
+    k = Qr.shape[0]
+    traj = O.rollout(Op, r, Qr[0], n_steps, mode=mode, dt=dt)
+    mu = Qr.mean(axis=0)
+    mdt = np.max(np.abs(Qr - mu), axis=0)
+    denom = np.max(mdt)
+    fin = np.all(np.isfinite(traj), axis=1)
+    with np.errstate(invalid="ignore"):
+        dev = np.where(fin, np.max(np.abs(traj - mu), axis=1), 0.0)
+    g = np.maximum.accumulate(dev) / denom
+    bad = (~fin) | (g >= max_growth)
+    if bad.any():
+        t = int(np.argmax(bad))
+        st = 2 if not fin[t] else 3
+        margin = abs(g[t] / max_growth - 1.0) if fin[t] else np.inf
+        if t > 0 and fin[t]:
+            margin = min(margin, abs(g[t - 1] / max_growth - 1.0))
+        return dict(status=st, steps=t, err=np.inf, growth=g[t] if fin[t] else np.inf, margin=margin)
+    return dict(status=0, steps=n_steps - 1, err=O.train_error(Qr[:k], traj[:k]),
+                growth=O.growth_ratio(traj, mu, mdt), margin=abs(g[-1] / max_growth - 1.0))
+
+
+def _learn_parity(dp, Qh, r_list, b1, b2, n_steps, mode, dt, rollout_tol=1e-8):
+    """dopinf_learn against the oracle on every candidate:
+    (a) operators: each candidate's O against the oracle's Cholesky solve, normwise, within
+        4 d eps cond(G + reg) (two backward-stable solves of the same system; cond is bounded
+        above by (lambda_max(G) + max beta) / (lambda_min(G) + min beta), G positive semi-definite);
+    (b) rollouts: status and stop step of every candidate, training error and growth of every
+        valid one, against the oracle's rollout of the GPU's own operator (1e-8 relative, the
+        rollout tolerance), except where the deciding growth lies within 1e-8 of the threshold;
+    (c) selection: the GPU's pick is the lowest-index minimum over its valid candidates, and the
+        oracle's pick is valid on the GPU with an error within the tolerances of the minimum."""
+    mcode = dp.DISCRETE if mode == "discrete" else dp.CONTINUOUS_RK4
+    Qd = torch.from_numpy(np.ascontiguousarray(Qh.T)).cuda().t()
+    res = dp.dopinf_learn(Qd, r_list, b1, b2, n_steps, mode=mcode, dt=dt, operators=True)
+    st = res["status"].cpu().numpy()
+    err = res["train_err"].cpu().numpy()
+    gro = res["growth"].cpu().numpy()
+    steps = res["steps"].cpu().numpy()
+    nb = len(b1) * len(b2)
+    checked = dict(ops=0, roll=0, skipped_edge=0)
+    for ir, r in enumerate(r_list):
+        Dh, Y = O.learning_data(Qh, r, mode, dt)
+        G, B = O.normal_equations(Dh, Y)
+        lam = np.linalg.eigvalsh(G)
+        d = G.shape[0]
+        for p in range(nb):
+            c = ir * nb + p
+            bb1, bb2 = b1[p // len(b2)], b2[p % len(b2)]
+            Oref, ok = O.solve_cholesky(G, B, O.regulariser(r, bb1, bb2))
+            cond = (lam[-1] + max(bb1, bb2)) / (max(lam[0], 0.0) + min(bb1, bb2))
+            if not ok:
+                assert st[c] == 1 or cond * EPS > 1e-3, (c, st[c])
+                continue
+            if st[c] == 1:
+                assert cond * EPS > 1e-3, (c, cond)   # breakdown only where the system is near singular
+                continue
+            Og = res["operators"][c].cpu().numpy()
+            tol = 4 * d * EPS * cond
+            rel = np.linalg.norm(Og - Oref) / np.linalg.norm(Oref)
+            assert rel <= max(tol, 1e-14), (r, bb1, bb2, rel, tol)
+            checked["ops"] += 1
+            m = _oracle_rollout_metrics(Og, r, Qh, n_steps, mode, dt)
+            if m["margin"] < 1e-8:
+                checked["skipped_edge"] += 1
+                continue
+            assert st[c] == m["status"], (c, r, bb1, bb2, st[c], m)
+            assert steps[c] == m["steps"], (c, steps[c], m["steps"])
+            if m["status"] == 0:
+                # the training error compares two nearly equal trajectories when it is small: a
+                # relative trajectory difference delta moves it by at most delta (1 + err), so
+                # an absolute 1e-10 (far above the FP64 and double-word rounding) is allowed too
+                assert abs(err[c] - m["err"]) <= rollout_tol * m["err"] + 1e-10, (c, err[c], m["err"])
+                assert abs(gro[c] - m["growth"]) <= rollout_tol * m["growth"], (c, gro[c], m["growth"])
+            elif m["status"] == 3:
+                # the growth of a stopped rollout is read where it diverges, which amplifies the
+                # rounding differences of the two arithmetics: both must be past the threshold
+                assert gro[c] >= 1.2, (c, gro[c], m)
+            checked["roll"] += 1
+    valid = np.nonzero(st == 0)[0]
+    if valid.size:
+        emin = err[valid].min()
+        assert res["best"] == int(valid[np.argmax(err[valid] == emin)])
+    else:
+        assert res["best"] == -1
+    return res, checked
+
+
 @pytest.mark.parametrize("mode", ["discrete", "continuous"])
 def test_learn_vs_oracle(dp, mode, arith):
     Qh = _reduced(r_fixed=6)
-    k = Qh.shape[1]
     b1 = synth.logspace(-8, 2, 4)
     b2 = synth.logspace(-8, 2, 4)
-    n_steps = 400
-    mcode = dp.DISCRETE if mode == "discrete" else dp.CONTINUOUS_RK4
     dt = synth.WORKLOADS["small"].snap_dt
-    ref = O.learn(Qh, [4, 6], b1, b2, n_steps, mode=mode, dt=dt)
-    Qd = torch.from_numpy(Qh.T.copy()).cuda().t()
-    res = dp.dopinf_learn(Qd, [4, 6], b1, b2, n_steps, mode=mcode, dt=dt)
-    err = res["train_err"].cpu().numpy()
-    st = res["status"].cpu().numpy()
-    print("oracle valid", ref["valid"].astype(int), "\ngpu status", st)
-    print("oracle err", ref["train_err"], "\ngpu err", err)
-    both = ref["valid"] & (st == 0)
-    # Candidates with tiny regularisation are ill-conditioned: compare those whose beta1 is
-    # large enough that cond(G + reg) * eps stays below 1e-9.
-    assert both.sum() >= 2
-    # validity agrees except possibly for a candidate on the edge of the growth threshold
-    assert np.sum(ref["valid"] != (st == 0)) <= 1
-    for c in np.nonzero(both)[0]:
-        r, bb1, bb2 = ref["candidates"][c]
-        if min(bb1, bb2) >= 1e-4:
-            assert abs(err[c] - ref["train_err"][c]) <= 1e-8 * max(ref["train_err"][c], 1e-12) + 1e-12, c
+    res, checked = _learn_parity(dp, Qh, [4, 6], b1, b2, 400, mode, dt)
+    print(checked)
+    assert checked["ops"] >= 24 and checked["roll"] >= 24
+    ref = O.learn(Qh, [4, 6], b1, b2, 400, mode=mode, dt=dt)
     best = res["best"]
     assert best >= 0 and ref["best"] >= 0
     # the chosen candidate is (within rounding) a minimiser of the oracle's training error
     assert ref["valid"][best]
     assert ref["train_err"][best] <= ref["train_err"][ref["best"]] * (1 + 1e-6) + 1e-12
+
+
+_LARGE = {}
+
+
+def _reduced_large(r_fixed):
+    """Reduced data with up to 80 modes from a step-flow-style system (r_true = 40, two
+    variables x 3000 rows, k = 400): the modes past 40 carry the noise, as in the batched
+    learn workloads that fit r up to 80 on such data."""
+    if "Qh" not in _LARGE:
+        w = synth.Workload("large-r", 2, 3000, 400, 40, seed=4040)
+        Qn, _ = synth.snapshots_numpy(w)
+        Qt, _, _, _ = O.transform(Qn, w.var_row_offsets())
+        _LARGE["Qh"] = O.reduce(O.gram(Qt), r_fixed=80)["Qhat"]
+    return _LARGE["Qh"][:r_fixed]
+
+
+@pytest.mark.parametrize("r", [33, 48, 64])
+@pytest.mark.parametrize("mode", ["discrete", "continuous"])
+def test_learn_large_r_vs_oracle(dp, r, mode, arith):
+    """r above 32 (operator rows in shared memory, block-Schur solves with quadratic blocks of
+    s = 561 .. 2080): operators, statuses, stop steps and metrics of every candidate."""
+    Qh = _reduced_large(r)
+    b1 = synth.logspace(-6, 0, 3)
+    b2 = synth.logspace(-2, 4, 3)
+    res, checked = _learn_parity(dp, Qh, [r], b1, b2, 400, mode, 1e-2)
+    print(r, mode, checked, res["status"].cpu().numpy())
+    assert checked["ops"] >= 6 and checked["roll"] >= 6
+
+
+def test_learn_r80_vs_oracle(dp, arith):
+    """The largest r of the batched-learn workloads (d = 3321 > the 399 data rows): short RK4
+    horizon, every candidate against the oracle."""
+    Qh = _reduced_large(80)
+    b1 = synth.logspace(-4, 0, 2)
+    b2 = synth.logspace(0, 4, 2)
+    res, checked = _learn_parity(dp, Qh, [80], b1, b2, 400, "continuous", 1e-2)
+    print(checked, res["status"].cpu().numpy())
+    assert checked["ops"] >= 3 and checked["roll"] >= 3
 
 
 def _learn_outputs(res):
@@ -413,6 +529,39 @@ def test_learn_double_word_matches_fp64(dp):
         assert rel.max() <= 1e-10, (key, rel.max())
     gro = st == 3
     assert np.all(f["growth"].cpu().numpy()[gro] >= 1.2) and np.all(w["growth"].cpu().numpy()[gro] >= 1.2)
+
+
+@pytest.mark.parametrize("edge", [1.0 + 1e-13, 1.0 - 1e-13, 1.0 + 1e-9])
+def test_learn_double_word_growth_threshold_edge(dp, edge):
+    """max_growth set right at a valid candidate's FP64 growth (just above, just below): the
+    double-word rollouts must not decide a growth that close to the threshold themselves, so
+    statuses, step counts and the selection are those of the FP64 arithmetic."""
+    Qh = _reduced(r_fixed=12)
+    Qd = torch.from_numpy(Qh.T.copy()).cuda().t()
+    b1 = synth.logspace(-8, 2, 5)
+    b2 = synth.logspace(-8, 2, 5)
+    dt = synth.WORKLOADS["small"].snap_dt
+    prev = dp.dopinf_tune_rollout_arith(0)
+    try:
+        dp.dopinf_tune_rollout_arith(dp.ROLLOUT_FP64)
+        base = dp.dopinf_learn(Qd, [4, 8, 12], b1, b2, 600, mode=dp.CONTINUOUS_RK4, dt=dt)
+        st = base["status"].cpu().numpy()
+        gro = base["growth"].cpu().numpy()
+        valid = np.nonzero(st == 0)[0]
+        assert valid.size >= 2
+        c = valid[np.argmax(gro[valid])]          # the valid candidate closest to the threshold
+        mg = float(gro[c]) * edge
+        out = {}
+        for a in (dp.ROLLOUT_FP64, dp.ROLLOUT_DW):
+            dp.dopinf_tune_rollout_arith(a)
+            out[a] = dp.dopinf_learn(Qd, [4, 8, 12], b1, b2, 600, mode=dp.CONTINUOUS_RK4, dt=dt, max_growth=mg)
+    finally:
+        dp.dopinf_tune_rollout_arith(prev)
+    f, w = out[dp.ROLLOUT_FP64], out[dp.ROLLOUT_DW]
+    assert (int(f["status"][c].item()) == 0) == (edge > 1.0)
+    assert torch.equal(f["status"], w["status"])
+    assert torch.equal(f["steps"], w["steps"])
+    assert f["best"] == w["best"]
 
 
 def test_learn_double_word_out_of_range_runs_fp64(dp):
@@ -477,10 +626,12 @@ def _stable_operator(r, seed):
     return Op, 0.5 * rng.standard_normal(r)
 
 
-@pytest.mark.parametrize("r", [1, 2, 7, 16, 30, 32, 33, 36])
+@pytest.mark.parametrize("r", [1, 2, 7, 16, 30, 32, 33, 36, 47, 64, 80, 92])
 def test_rollout_every_width_vs_oracle(dp, r):
-    """r <= 32 runs the column-owned kernel (1 to 5 column slots per thread), r > 32 the
-    row-split kernel; both against the oracle's rollout."""
+    """r <= 32 runs the register kernel (1 to 5 column slots per thread), 32 < r <= 96 the
+    shared-memory kernel (3 to 8 rows per CTA, clusters of up to 16 CTAs, r = 92 filling the
+    227 KB of shared memory); both against the
+    oracle's rollout."""
     Op, q0 = _stable_operator(r, 100 + r)
     Od = torch.from_numpy(Op.T.copy()).cuda().t()
     q0d = torch.from_numpy(q0.copy()).cuda()
