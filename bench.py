@@ -7,8 +7,9 @@ with 5000-step RK4 rollouts (continuous mode, snapshot spacing 0.01).
 
 Contract: prints ONE JSON line (rank 0).  value = whole-job pipelines per second (inputs
 resident in HBM), e2e = the same through the C ABI with the snapshot matrix copied from
-pinned host memory every step and the results copied back.  --impl reference times the FP64
-CPU oracle on a bounded sample of the same workload.
+pinned host memory every step and the results copied back.  --impl reference runs the FP64
+CPU oracle over one whole pipeline of the same workload, its parts dealt out over the timed
+steps (nothing extrapolated).
 """
 import argparse
 import dataclasses
@@ -29,6 +30,9 @@ METRIC = "Gram TFLOP/s + dOpInf learn time, split-prec/batched vs FP64 plain, at
 UNIT = "dOpInf pipelines/s"
 WORKLOAD = "stepflow"
 FP64_NOMINAL_TF, BF16_NOMINAL_TF = 1.25, 2250.0
+# DRAM bytes (read + write) per launch of the r = 30 rollout launch, from the ncu captures
+# summarised in profiles/ (None: not captured for the current kernel)
+ROLLOUT_TRAFFIC = {"dw": 8.3e6, "fp64": None}
 
 
 def parse():
@@ -50,6 +54,9 @@ def parse():
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential grid-search baseline")
     p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch schedules")
+    p.add_argument("--no-extras", action="store_true", help="skip the paper-shaped and batched-learn extras")
+    p.add_argument("--batched-problems", type=int, default=8,
+                   help="problems of the batched-learn extra (the configuration has 512)")
     p.add_argument("--n-steps", type=int, default=0, help="override the rollout length of --stage learn")
     p.add_argument("--r-list", default="", help="override the r list of --stage learn, e.g. 30 or 10,20")
     p.add_argument("--rows-large", type=int, default=0, help="--stage learn: rollout rows per CTA for r > 32 (3..8; 0: default)")
@@ -118,53 +125,134 @@ class Clocks:
 
 
 # ------------------------------------------------------------------------------------ oracle
-def oracle_sample(w):
-    """Times the FP64 CPU oracle on a bounded sample; returns (seconds per full pipeline, desc)."""
+def _oracle_learn_one(args):
+    """One Step IV candidate through the oracle (a worker of the spawned pool)."""
     from oracle import dopinf_oracle as O
-    from paper_2504_14338_gb300 import synth
-    frac = 16
-    ws = dataclasses.replace(w, name=w.name + "-sample", n_per_var=w.n_per_var // frac)
-    Qn, _ = synth.snapshots_numpy(ws)
+    Qhat, r, b1, b2, n_steps, mode, dt = args
     t0 = time.perf_counter()
-    Qt, _, _, _ = O.transform(Qn, ws.var_row_offsets())
-    t1 = time.perf_counter()
-    D = O.gram(Qt)
-    t2 = time.perf_counter()
-    r_max = max(w.r_list)
-    red = O.reduce(D, r_fixed=r_max)
-    t3 = time.perf_counter()
-    b1, b2 = w.beta1s(), w.beta2s()
-    t_learn = 0.0
-    for r in w.r_list:  # two candidates per r from the middle of the grid
-        s = time.perf_counter()
-        O.learn(red["Qhat"], [r], [b1[len(b1) // 2]], b2[len(b2) // 2 - 1:len(b2) // 2 + 1], w.n_steps,
-                mode=w.mode, dt=w.snap_dt)
-        t_learn += (time.perf_counter() - s) * len(b1) * len(b2) / 2
-    per_pipeline = frac * ((t1 - t0) + (t2 - t1)) + (t3 - t2) + t_learn
-    desc = ("Steps II-III on 1/%d of the rows (n=%d, k=%d), scaled x%d; full reduce; Step IV on two (beta1, "
-            "beta2) per r (%d-step %s rollouts), scaled x%d; oracle as committed (numpy FP64)" % (
-                frac, ws.n, w.k, frac, w.n_steps, w.mode, len(b1) * len(b2) // 2))
-    return per_pipeline, desc, time.perf_counter() - t0
+    out = O.learn(Qhat, [r], [b1], [b2], n_steps, mode=mode, dt=dt)
+    return float(out["train_err"][0]), bool(out["valid"][0]), time.perf_counter() - t0
+
+
+class OraclePipeline:
+    """The FP64 CPU oracle as committed, run over one whole pipeline of a workload (Steps II-IV,
+    every candidate, rollouts to the end as in the paper) as a sequence of parts in the
+    pipeline's order: the transform, the Gram as a sum of row-block products (the paper's
+    partitioned Gram, eq. mos_partitioned), the eigensolve and projection, then the Step IV
+    candidates in groups, each group spread over a pool of worker processes (one candidate per
+    task).  Nothing is extrapolated: the parts of one pipeline are all timed.  The Gram's matrix
+    products use numpy's BLAS threads; each rollout is one Python thread."""
+
+    def __init__(self, Qn, w, workers=None, gram_blocks=8, learn_groups=16):
+        import multiprocessing as mp
+        self.Qn, self.w = Qn, w
+        self.workers = workers or max(1, min(16, os.cpu_count() or 1))
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+        n = Qn.shape[0]
+        self.row_blocks = [(n * j // gram_blocks, n * (j + 1) // gram_blocks) for j in range(gram_blocks)]
+        self.cands = [(r, b1, b2) for r in w.r_list for b1 in w.beta1s() for b2 in w.beta2s()]
+        ng = max(1, min(learn_groups, len(self.cands)))
+        self.groups = [self.cands[len(self.cands) * j // ng: len(self.cands) * (j + 1) // ng] for j in range(ng)]
+        self.parts = (["transform"] + ["gram %d" % j for j in range(gram_blocks)] + ["reduce"]
+                      + ["learn %d" % j for j in range(ng)])
+
+    def close(self):
+        self.pool.terminate()
+
+    def warm(self):
+        """Starts the workers (imports) with one short oracle call each."""
+        Qh = np.random.default_rng(0).standard_normal((3, 10))
+        self.pool.map(_oracle_learn_one, [(Qh, 2, 1e-2, 1e-2, 10, "discrete", 1.0)] * self.workers)
+
+    def run_part(self, i, st):
+        from oracle import dopinf_oracle as O
+        name = self.parts[i]
+        w = self.w
+        if name == "transform":
+            st["Q"], _, _, _ = O.transform(self.Qn, w.var_row_offsets())
+            st["D"] = np.zeros((w.k, w.k))
+        elif name.startswith("gram"):
+            a, b = self.row_blocks[int(name.split()[1])]
+            st["D"] += O.gram(st["Q"][a:b])
+        elif name == "reduce":
+            st["red"] = O.reduce(st["D"], r_fixed=max(w.r_list))
+            st["learn"] = []
+        else:
+            mode = w.mode
+            tasks = [(st["red"]["Qhat"], r, b1, b2, w.n_steps, mode, w.snap_dt)
+                     for (r, b1, b2) in self.groups[int(name.split()[1])]]
+            st["learn"].extend(self.pool.map(_oracle_learn_one, tasks))
+
+    def describe(self):
+        w = self.w
+        return ("one whole pipeline of the workload through the oracle as committed (numpy FP64): transform, "
+                "Gram as the sum of %d row-block products (BLAS on %d host threads), eigensolve and projection, "
+                "all %d Step IV candidates with %d-step %s rollouts run to the end (no early exit, as in the "
+                "paper), one candidate per task over %d worker processes; every part timed, nothing extrapolated"
+                % (len(self.row_blocks), os.cpu_count() or 1, len(self.cands), w.n_steps, w.mode, self.workers))
+
+
+def oracle_full_pipeline(Qn, w, workers=None):
+    """Times one whole oracle pipeline; returns (seconds, per-part seconds, description, workers)."""
+    op = OraclePipeline(Qn, w, workers)
+    try:
+        op.warm()
+        st, times = {}, {}
+        t0 = time.perf_counter()
+        for i, name in enumerate(op.parts):
+            s = time.perf_counter()
+            op.run_part(i, st)
+            times[name] = time.perf_counter() - s
+        total = time.perf_counter() - t0
+        return total, times, op.describe(), op.workers
+    finally:
+        op.close()
 
 
 def run_reference(args):
+    """The oracle on the GPU arm's workload: the K timed steps together run exactly one whole
+    pipeline (its parts dealt out in order over the steps), so ms_per_step x steps is the time
+    of one pipeline and value = 1 / that time; the W warm-up steps each run one untimed
+    Step IV candidate."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from paper_2504_14338_gb300 import synth
     w = workload(args.workload)
-    times = []
-    desc = ""
-    for i in range(args.warmup + args.steps):
-        per, desc, _ = oracle_sample(w)
-        if i >= args.warmup:
-            times.append(per)
-    sec = float(np.mean(times))
+    Qn, _ = synth.snapshots_numpy(w)
+    op = OraclePipeline(Qn, w)
+    try:
+        op.warm()
+        # warm-up: single candidates of the smallest r (no timing)
+        st_w = {}
+        Qh_small = np.random.default_rng(1).standard_normal((max(w.r_list), w.k))
+        for _ in range(args.warmup):
+            _oracle_learn_one((Qh_small, min(w.r_list), w.beta1s()[-1], w.beta2s()[-1], w.k, w.mode, w.snap_dt))
+        del st_w
+        P = len(op.parts)
+        K = max(1, args.steps)
+        bounds = [P * j // K for j in range(K + 1)]
+        st, per_step = {}, []
+        t_all = time.perf_counter()
+        for j in range(K):
+            s = time.perf_counter()
+            for i in range(bounds[j], bounds[j + 1]):
+                op.run_part(i, st)
+            per_step.append(time.perf_counter() - s)
+        total = time.perf_counter() - t_all
+        desc = op.describe() + "; the %d timed steps together are that one pipeline" % K
+        workers = op.workers
+    finally:
+        op.close()
     cores = os.cpu_count()
-    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / sec, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+    value = 1.0 / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
-            "cpu_baseline": {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
-            "e2e": {"value": 1.0 / sec, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "workers": workers, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "pipeline_s": total, "step_s": per_step}
     print(json.dumps(line), flush=True)
 
 
@@ -272,6 +360,115 @@ def gram_modes_measure(dp, Q, D_pipe, pipe_name, pipe_ms, ws):
             "%s_ms" % pipe_name: pipe_ms, "%s_max_rel_vs_fp64_pipe" % pipe_name: dev(D_pipe),
             "bf16x4_ms": t16, "bf16x4_max_rel_vs_fp64_pipe": dev(D16),
             "speedup_%s_vs_fp64_pipe" % pipe_name: t64 / pipe_ms}
+
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def paper_shape_measure(dp, synth, dev, reps=3):
+    """The paper's tutorial shape (n = 2 x 146,339 rows, k = 600, r by the 0.9996 energy rule,
+    the 8 x 8 grid of Section 4, 1200-step discrete rollouts) through the GPU pipeline: the
+    device time of Steps II-IV, and the same with the snapshot matrix uploaded from pinned host
+    memory first.  The paper's 8.35 s (one CPU core of a 256-core node, HDF5 loading included)
+    is quoted beside it as context only."""
+    import torch
+    w = synth.WORKLOADS["paper"]
+    QT = synth.snapshots_torch(w, dev)
+    host = torch.empty(QT.shape, dtype=QT.dtype, pin_memory=True)
+    host.copy_(QT)
+    Q = QT.t()
+    ws = dp.Workspace(dev)
+    stream = torch.cuda.current_stream()
+    b1, b2 = w.beta1s(), w.beta2s()
+    out = []
+    for i in range(reps + 1):
+        e = _events(6)
+        e[0].record(stream)
+        QT.copy_(host, non_blocking=True)
+        e[1].record(stream)
+        dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
+        e[2].record(stream)
+        D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws)
+        e[3].record(stream)
+        red = dp.dopinf_reduce(D, r_cap=30, energy_target=0.9996, ws=ws)
+        e[4].record(stream)
+        res = dp.dopinf_learn(red["Qhat"], [red["r"]], b1, b2, w.n_steps, mode=dp.DISCRETE, ws=ws)
+        e[5].record(stream)
+        torch.cuda.synchronize()
+        if i:
+            out.append([e[j].elapsed_time(e[j + 1]) for j in range(5)])
+    m = np.median(np.array(out), axis=0)
+    st = res["status"].cpu().numpy()
+    return {"workload": "paper: n=2x146339=292678, k=600, r by energy 0.9996, 8x8 grid logspace(-10,0,8) x "
+                        "logspace(-4,4,8), 1200-step discrete rollouts, f64",
+            "r": red["r"], "best": res["best"], "valid": int((st == 0).sum()),
+            "stages_ms": {"upload": m[0], "transform": m[1], "gram": m[2], "reduce": m[3], "learn": m[4]},
+            "steps_ii_iv_ms": float(m[1:].sum()), "with_upload_ms": float(m.sum()),
+            "paper_s_context": {"value": 8.35, "what": "Steps I-IV, p = 1, one core of a 256-core AMD EPYC 7702 node, "
+                                                      "HDF5 loading included (Section 4)"}}
+
+
+def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16):
+    """The batched learn configuration on a stated subset: n_problems of its 512 problems (r drawn
+    from U{10..80} with a fixed seed; reduced data of k = 1500 from step-flow-style generators,
+    r_true = 40, each problem its own seed), each with the 16 x 16 grid and 10,000-step RK4
+    rollouts, all captured into one CUDA graph (one branch per problem) and replayed once.
+    Against it: the unbatched path, one candidate at a time (one dopinf_learn call each, no
+    graph), timed on n_sub of each problem's 256 candidates (the grid diagonal) and scaled to 256."""
+    import torch
+    from paper_2504_14338_gb300.graph import BatchedLearnGraph
+    rng = np.random.default_rng(20250417)
+    r_draw = rng.integers(10, 81, size=512)
+    rs = [int(x) for x in r_draw[:n_problems]]
+    b1 = synth.logspace(-10.0, 0.0, 16)
+    b2 = synth.logspace(-4.0, 4.0, 16)
+    ws = dp.Workspace(dev)
+    problems = []
+    for p, r in enumerate(rs):
+        w = synth.Workload("batched-%d" % p, 2, 4000, 1500, 40, seed=30_000 + p)
+        Q = synth.snapshots_torch(w, dev).t()
+        dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
+        D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws)
+        red = dp.dopinf_reduce(D, r_cap=r, r_fixed=r, ws=ws)
+        problems.append(dict(Qhat=red["Qhat"].clone(memory_format=torch.preserve_format), r_list=[r], beta1=b1,
+                             beta2=b2))
+        del Q, D
+    dt = 0.01
+    n_steps = 10_000
+    bg = BatchedLearnGraph(problems, n_steps, mode=dp.CONTINUOUS_RK4, dt=dt).capture()
+    stream = torch.cuda.current_stream()
+    e = _events(2)
+    e[0].record(stream)
+    bg.replay()
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e[0].elapsed_time(e[1])
+    flops, valid = 0, 0
+    for pr, out in zip(problems, bg.out):
+        r = pr["r_list"][0]
+        d = r + r * (r + 1) // 2 + 1
+        flops += int(out["steps"].sum().item()) * 4 * 2 * r * d
+        valid += int((out["status"] == 0).sum().item())
+    # the unbatched baseline on the grid diagonal of every problem
+    t0 = time.perf_counter()
+    for pr in problems:
+        for i in range(n_sub):
+            j = i * 16 // n_sub
+            dp.dopinf_learn(pr["Qhat"], pr["r_list"], [b1[j]], [b2[j]], n_steps, mode=dp.CONTINUOUS_RK4, dt=dt, ws=ws)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3 * (256 / n_sub)
+    del bg
+    torch.cuda.empty_cache()
+    return {"workload": "batched learn, %d of 512 problems: r=%s, 16x16 grid, k=1500, 10000-step RK4, f64, one graph"
+                        % (n_problems, rs),
+            "batched_ms": batched_ms, "problems_per_s": n_problems / (batched_ms / 1e3),
+            "rollout_fp64_gflops": flops / (batched_ms / 1e3) / 1e9, "valid_candidates": valid,
+            "n_candidates": 256 * n_problems,
+            "sequential_ms_est": seq_ms, "speedup_vs_sequential": seq_ms / batched_ms,
+            "sequential_how": "one dopinf_learn call per candidate (no graph), timed on %d of each problem's 256 "
+                              "candidates (the grid diagonal), scaled x%.0f" % (n_sub, 256 / n_sub)}
 
 
 def sequential_learn_measure(dp, Qhat, w, mode):
@@ -548,8 +745,8 @@ def main():
     roof.update({
         # DRAM bytes of one ncu capture of the r = 30 launch on the same r, k, grid and horizon
         # (the rollout's work does not depend on n): the operators, read once
-        "traffic": 8.3e6, "traffic_scope": "the r = 30 launch alone (the stage's largest; its operators, "
-                                            "7.6 MB, read once)",
+        "traffic": ROLLOUT_TRAFFIC.get("fp64" if arith == dp.ROLLOUT_FP64 else "dw"),
+        "traffic_scope": "the r = 30 launch alone (the stage's largest; its operators, 7.6 MB, read once)",
         "traffic_source": "profiles/rollout_cols_kernel_stepflow_learn.md",
         "algorithmic_flops_per_launch": roll_flops, "launch_ms": roll_ms,
         "rhs_evaluations": int(steps_run.sum()) * evals,
@@ -583,9 +780,16 @@ def main():
     launches = 3 + gram_launches + 9 + (1 + 6 * len(w.r_list) + schur + roll_launches + 2)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        per, desc, wall = oracle_sample(w)
-        cpu = {"value": 1.0 / per, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
-               "sample_wall_s": wall}
+        # one whole oracle pipeline on the same raw snapshots (the pinned host copy when there is one)
+        Qn = host_raw.numpy().T if host_raw is not None else synth.snapshots_numpy(w)[0]
+        total, parts, desc, workers = oracle_full_pipeline(Qn, w)
+        del Qn
+        cpu = {"value": 1.0 / total, "unit": UNIT, "cores": os.cpu_count(), "workers": workers, "kind": "oracle",
+               "sample": desc, "pipeline_s": total,
+               "parts_s": {"transform": parts["transform"],
+                           "gram": sum(v for k_, v in parts.items() if k_.startswith("gram")),
+                           "reduce": parts["reduce"],
+                           "learn": sum(v for k_, v in parts.items() if k_.startswith("learn"))}}
     split = None
     if rank == 0 and not args.no_split and args.stage == "all" and not args.n_per_var:
         del QT, Q
@@ -595,26 +799,39 @@ def main():
     if rank == 0 and not args.no_sequential:
         seq_ms = sequential_learn_measure(dp, red_last["Qhat"], w, mode)
         seq = {"sequential_ms": seq_ms, "batched_ms": stage["learn"], "speedup": seq_ms / stage["learn"]}
-    # the learn step once more with FP64 rollouts, for reading the default double-word ones
-    # against (time, selected candidate, training errors of the valid candidates)
-    fp64_roll = None
+    # the learn step once more with double-word rollouts (FP32 pairs, ~48 bits; statuses handed
+    # to FP64 near the decisions), read against the FP64 step: time, pick, statuses, errors
+    dw_roll = None
     if rank == 0 and not args.no_sequential:
-        prev = dp.dopinf_tune_rollout_arith(dp.ROLLOUT_FP64)
+        prev = dp.dopinf_tune_rollout_arith(dp.ROLLOUT_DW)
         try:
             for _ in range(2):
-                r64 = dp.dopinf_learn(red_last["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode,
+                rdw = dp.dopinf_learn(red_last["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode,
                                       dt=w.snap_dt, ws=ws)
-            e_dw, e64 = res["train_err"].cpu().numpy(), r64["train_err"].cpu().numpy()
+            e64, e_dw = res["train_err"].cpu().numpy(), rdw["train_err"].cpu().numpy()
             ok = np.isfinite(e64) & np.isfinite(e_dw)
-            fp64_roll = {"rollouts_ms": r64["stage_ms"]["rollouts"], "best": r64["best"],
-                         "same_best": r64["best"] == res["best"],
-                         "same_status": bool(np.array_equal(r64["status"].cpu().numpy(), res["status"].cpu().numpy())),
-                         "max_rel_train_err_diff_valid": float(np.max(np.abs(e_dw[ok] - e64[ok]) / e64[ok])) if ok.any()
-                         else None}
+            dw_roll = {"rollouts_ms": rdw["stage_ms"]["rollouts"], "fp64_rollouts_ms": roll_ms, "best": rdw["best"],
+                       "same_best": rdw["best"] == res["best"],
+                       "same_status": bool(np.array_equal(rdw["status"].cpu().numpy(), res["status"].cpu().numpy())),
+                       "same_steps": bool(np.array_equal(rdw["steps"].cpu().numpy(), res["steps"].cpu().numpy())),
+                       "max_rel_train_err_diff_valid": float(np.max(np.abs(e_dw[ok] - e64[ok]) / e64[ok])) if ok.any()
+                       else None}
         except Exception as ex:  # reported, never fatal for the line
-            fp64_roll = {"error": str(ex)}
+            dw_roll = {"error": str(ex)}
         finally:
             dp.dopinf_tune_rollout_arith(prev)
+    paper = None
+    if rank == 0 and not args.no_extras:
+        try:
+            paper = paper_shape_measure(dp, synth, dev)
+        except Exception as ex:
+            paper = {"error": str(ex)}
+    batched = None
+    if rank == 0 and not args.no_extras:
+        try:
+            batched = batched_learn_measure(dp, synth, dev, n_problems=args.batched_problems)
+        except Exception as ex:
+            batched = {"error": str(ex)}
     if rank == 0:
         best = res["best"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -629,9 +846,10 @@ def main():
                                "reduce": "f64", "learn_solves": "f64",
                                "rollouts": ("f32 double-word (~48 bits), statuses as in f64"
                                             if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else "f64")},
+                "timing": "CUDA events on the launching stream around the timed steps; inputs larger than L2",
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq,
-                "learn_fp64_rollouts": fp64_roll}
+                "learn_double_word_rollouts": dw_roll, "paper_shape": paper, "batched_learn": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -86,6 +86,19 @@ const char* dopinf_status_string(int status);
  * valid until the next failing call of the same thread. */
 const char* dopinf_last_error(void);
 
+/* Test of the error paths (no counterpart in the paper): which = DOPINF_TEST_GRID_BARRIER
+ * withholds the release of the cooperative tridiagonalisation's grid barrier (dopinf_reduce),
+ * DOPINF_TEST_TENSOR_GRAM keeps the MMA issuer of the tensor-core Grams (BF16X4, and the first
+ * digit pass of OZAKI_FP64) from releasing its pipeline stages.  The bounded waits that depend
+ * on them then expire at their limit (about 2 s each); the kernels wind down (their copies and
+ * MMAs in flight are waited for, tensor memory is released), the calls report
+ * DOPINF_E_TIMEOUT or DOPINF_FLAG_TIMEOUT, and the context stays usable.  which = 0 restores
+ * normal operation; which < 0 only queries.  Returns the previous value.  Process-wide; for
+ * tests only. */
+#define DOPINF_TEST_GRID_BARRIER 1
+#define DOPINF_TEST_TENSOR_GRAM 2
+int dopinf_test_expire_waits(int which);
+
 /* ------------------------------------------------------------------------------------
  * Step II (Section 3.3): centre each row by its temporal mean, then divide each variable
  * block by the largest |centred value| of the block.
@@ -122,15 +135,16 @@ int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
  *   and D ~= H^T H + H^T L + L^T H + L^T L on the tcgen05 tensor cores: FP32 accumulation
  *   over 128-row chunks with H^T H in columns of its own, a compensated FP32 (TwoSum) running
  *   sum per work unit, FP64 sum of the units (|e| <= 2^-17 |x|).  Requires k <= 65535.
- *   Synchronises the stream; returns DOPINF_E_TIMEOUT if an internal bounded wait expired
- *   (D is then not valid).
+ *   Synchronises the stream; returns DOPINF_E_TIMEOUT if an internal bounded wait expired,
+ *   DOPINF_E_NONFINITE if Q holds a NaN or Inf (D is then not valid).
  * DOPINF_GRAM_OZAKI_FP64: column a is scaled by 2^-s_a (|x| < 2^(s_a - 1) on the column) and
  *   cut into 7 balanced integer digits of 8 bits (|d| <= 128, exact in BF16):
  *   x = 2^s_a sum_i d_i 2^(-8 i) + e, |e| <= 2^(s_a - 57).  The 28 digit products of weight
  *   2..8 are summed on the tensor cores
  *   in row chunks whose partial sums are integers below 2^24 (exact), carried exactly by FP32
  *   TwoSum pairs and combined in FP64: an FP64-accurate D (the method of Ozaki et al. 2012).
- *   Requires k <= 65535.  Synchronises the stream; may return DOPINF_E_TIMEOUT.
+ *   Requires k <= 65535.  Synchronises the stream; may return DOPINF_E_TIMEOUT, or
+ *   DOPINF_E_NONFINITE if Q holds a NaN or Inf (D is then not valid).
  * Workspace: dopinf_gram_workspace(n, k, dtype, mode) bytes (BF16X4: 4 n k bytes of
  *   slices plus the per-unit FP64 partial tiles; OZAKI_FP64: 14 n k bytes of digits plus
  *   7 partial tiles per unit).
@@ -148,8 +162,9 @@ int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int
                 int accumulate, double* D, int64_t ldd, void* ws, size_t ws_bytes,
                 void* stream);
 /* The same product without any synchronisation (every mode; capturable into a CUDA graph):
- * a bounded wait that expired inside a tensor-core kernel ORs DOPINF_FLAG_TIMEOUT into the
- * device word *dev_flags (required) instead of returning DOPINF_E_TIMEOUT. */
+ * a bounded wait that expired inside a tensor-core kernel ORs DOPINF_FLAG_TIMEOUT, and NaN or
+ * Inf met by a tensor-core mode ORs DOPINF_FLAG_NONFINITE, into the device word *dev_flags
+ * (required) instead of returning DOPINF_E_TIMEOUT / DOPINF_E_NONFINITE. */
 int dopinf_gram_async(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
                       int accumulate, double* D, int64_t ldd, unsigned* dev_flags, void* ws,
                       size_t ws_bytes, void* stream);
@@ -265,7 +280,7 @@ int dopinf_tune_rollout_rows(int rows);
  * resident); other values only query.  Returns the previous value.  Process-wide.  The
  * results do not depend on it. */
 int dopinf_tune_rollout_rows_large(int rows);
-/* Rollout arithmetic of dopinf_learn: DOPINF_ROLLOUT_FP64 or DOPINF_ROLLOUT_DW (default); other
+/* Rollout arithmetic of dopinf_learn: DOPINF_ROLLOUT_FP64 (default, the paper's) or DOPINF_ROLLOUT_DW; other
  * values only query.  Returns the previous value.  Process-wide. */
 int dopinf_tune_rollout_arith(int arith);
 size_t dopinf_learn_workspace(int r_max, int64_t k, const int* r_list, int n_r, int n_b1,

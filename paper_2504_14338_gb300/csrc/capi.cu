@@ -14,7 +14,15 @@ namespace {
 __global__ void flag_if_set_kernel(const unsigned* err, unsigned* flags, unsigned bits) {
   if (*err) atomicOr(flags, bits);
 }
+__global__ void flag_status_kernel(const unsigned* err, unsigned* flags) {
+  const unsigned e = *err;
+  if (e & ~kErrNonfinite) atomicOr(flags, DOPINF_FLAG_TIMEOUT);
+  if (e & kErrNonfinite) atomicOr(flags, DOPINF_FLAG_NONFINITE);
+}
+int g_test_stall = 0;
 }  // namespace
+
+int test_stall() { return g_test_stall; }
 
 void flag_if_set(const unsigned* err, unsigned* flags, unsigned bits, cudaStream_t st) {
   flag_if_set_kernel<<<1, 1, 0, st>>>(err, flags, bits);
@@ -22,18 +30,27 @@ void flag_if_set(const unsigned* err, unsigned* flags, unsigned bits, cudaStream
 
 int finish_timeout(const unsigned* err, unsigned* dev_flags, cudaStream_t st) {
   if (dev_flags) {
-    flag_if_set(err, dev_flags, DOPINF_FLAG_TIMEOUT, st);
+    flag_status_kernel<<<1, 1, 0, st>>>(err, dev_flags);
     return launch_status();
   }
   unsigned e = 0;
   DOPINF_CUDA(cudaMemcpyAsync(&e, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   DOPINF_CUDA(cudaStreamSynchronize(st));
-  if (e) set_last_error("a bounded wait inside a tensor-core kernel", cudaErrorTimeout);
-  return e ? DOPINF_E_TIMEOUT : DOPINF_OK;
+  if (e & ~kErrNonfinite) {
+    set_last_error("a bounded wait inside a tensor-core kernel", cudaErrorTimeout);
+    return DOPINF_E_TIMEOUT;
+  }
+  return (e & kErrNonfinite) ? DOPINF_E_NONFINITE : DOPINF_OK;
 }
 }  // namespace dopinf
 
 DOPINF_API const char* dopinf_last_error(void) { return dopinf::g_last_error; }
+
+DOPINF_API int dopinf_test_expire_waits(int which) {
+  const int prev = dopinf::g_test_stall;
+  if (which >= 0) dopinf::g_test_stall = which & (dopinf::kStallGridBarrier | dopinf::kStallTensorGram);
+  return prev;
+}
 
 DOPINF_API const char* dopinf_status_string(int status) {
   switch (status) {

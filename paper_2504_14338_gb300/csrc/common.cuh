@@ -49,8 +49,17 @@ inline int launch_status() {
 
 // *flags |= bits if *err is non-zero (device-side status hand-off, no synchronisation).
 void flag_if_set(const unsigned* err, unsigned* flags, unsigned bits, cudaStream_t st);
-// Finish a call that left a device error word: flag it (asynchronous) or read it back.
+// Bit of a kernel error word that reports NaN/Inf in the data; its other bits report an
+// expired bounded wait.
+constexpr unsigned kErrNonfinite = 0x100u;
+// Finish a call that left a device error word: flag it (asynchronous: DOPINF_FLAG_TIMEOUT /
+// DOPINF_FLAG_NONFINITE into *dev_flags) or read it back (DOPINF_E_TIMEOUT, else
+// DOPINF_E_NONFINITE).
 int finish_timeout(const unsigned* err, unsigned* dev_flags, cudaStream_t st);
+// Test knob of the error paths (dopinf_test_expire_waits): bits of the bounded waits whose
+// signal is withheld, so that they expire.
+constexpr int kStallGridBarrier = 1, kStallTensorGram = 2;
+int test_stall();
 
 inline bool misaligned(const void* p, size_t a = kAlign) {
   return (reinterpret_cast<uintptr_t>(p) % a) != 0;

@@ -142,7 +142,9 @@ __device__ __forceinline__ uint64_t gtimer_ns() {
   return t;
 }
 
-__device__ bool grid_sync(GridBar* b) {
+// stall = 1 (a test of the error path) withholds the release: the arrivals can never reach
+// the count it waits for, so every wait runs into its limit.
+__device__ bool grid_sync(GridBar* b, unsigned stall) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -150,7 +152,7 @@ __device__ bool grid_sync(GridBar* b) {
     volatile unsigned* verr = &b->err;
     const unsigned g = *vgen;
     __threadfence();
-    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1 + stall) {
       atomicExch(&b->count, 0u);
       __threadfence();
       atomicAdd(&b->gen, 1u);
@@ -205,7 +207,7 @@ __device__ void reflector_inplace(double* x, int64_t k, int64_t j, double* sh, d
 // every update is also written through to A, where the next step's column and the reflectors
 // are read by everyone.
 __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, double* d, double* e, double* tau,
-                                                      double* pg, GridBar* bar, int resident) {
+                                                      double* pg, GridBar* bar, int resident, unsigned stall) {
   extern __shared__ double smd[];
   double* vj = smd;          // v_j (rows j+1..k-1)
   double* pj = smd + k;      // p_j
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
         if (lane == 0) pg[c] = tn * s;
       }
     }
-    if (!grid_sync(bar)) return;
+    if (!grid_sync(bar, stall)) return;
     // (e) p_{j+1} to shared memory, v_{j+1} becomes the pending reflector
     for (int64_t r = c1 + 1 + threadIdx.x; r < k; r += blockDim.x) pj[r] = tn != 0.0 ? __ldcg(pg + r) : 0.0;
     for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) vj[r] = vn[r];
@@ -710,7 +712,8 @@ int tridiagonalise(const ReduceWs& w, int64_t k, cudaStream_t st) {
       double *d = w.d, *e = w.e, *tau = w.tau, *p = w.p;
       GridBar* bar = w.bar;
       int64_t kk = k;
-      void* args[] = {&A, &kk, &d, &e, &tau, &p, &bar, &resident};
+      unsigned stall = (test_stall() & kStallGridBarrier) ? 1u : 0u;
+      void* args[] = {&A, &kk, &d, &e, &tau, &p, &bar, &resident, &stall};
       DOPINF_CUDA(cudaLaunchCooperativeKernel((const void*)hh_tridiag_coop, dim3((unsigned)grid), dim3(TB), args, smem, st));
       return launch_status();  // the barrier's error word is read with the results
     }

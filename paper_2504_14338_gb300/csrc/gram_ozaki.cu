@@ -56,6 +56,7 @@ struct OzShape {
   int64_t n, nrb, ncb;
   int k, tn, ntiles, splits, units;
   int64_t rows_per_split;
+  int stall;  // test of the error path: the MMA issuer of the first pass never releases a stage
 };
 
 __host__ __device__ inline void tile_of(int t, int tn, int& ta, int& tb) {
@@ -104,7 +105,8 @@ __device__ __forceinline__ void decode(float x, bool& neg, unsigned long long& m
 // max |Q[:, a]| per column, as s_a = 1 + the exponent e with max < 2^e (0 for an all-zero column).
 // Magnitudes compare as integers of their encodings.
 template <typename T>
-__global__ void __launch_bounds__(256) colmax_kernel(const T* __restrict__ Q, int64_t n, int64_t ldq, int* __restrict__ sexp) {
+__global__ void __launch_bounds__(256) colmax_kernel(const T* __restrict__ Q, int64_t n, int64_t ldq, int* __restrict__ sexp,
+                                                     unsigned* __restrict__ err) {
   __shared__ unsigned long long sh[256];
   const int64_t a = blockIdx.x;
   const T* q = Q + a * ldq;
@@ -137,6 +139,13 @@ __global__ void __launch_bounds__(256) colmax_kernel(const T* __restrict__ Q, in
     unsigned long long mx = 0;
     for (int i = 0; i < (int)blockDim.x; ++i) mx = sh[i] > mx ? sh[i] : mx;
     int e = 0;
+    // NaN or Inf (an all-ones exponent field): reported through the error word, and the column
+    // is digitised as if it were zero (D is then not valid)
+    const unsigned long long inf_bits = sizeof(T) == 8 ? 0x7ff0000000000000ull : 0x7f800000ull;
+    if (mx >= inf_bits) {
+      atomicOr(err, kErrNonfinite);
+      mx = 0;
+    }
     if (mx) {
       bool neg;
       unsigned long long m;
@@ -226,6 +235,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int plo = pair_lo(w), phi = pair_hi(w);
   const int64_t chunk_rows = chunk_rows_of(w);
   const int64_t plane_blocks = sh.nrb * sh.ncb;
+  __shared__ int skip_sh;
+  // a bounded wait of an earlier pass expired: D is not valid, the later passes stop at once
+  if (threadIdx.x == 0) skip_sh = (w > W_MIN && (*reinterpret_cast<volatile unsigned*>(err) & ~kErrNonfinite)) ? 1 : 0;
+  __syncthreads();
+  if (skip_sh) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -321,7 +335,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
               issued = true;
               first = false;
-              mma_commit(&empty_bar[stage]);
+              if (!(sh.stall && w == W_MIN)) mma_commit(&empty_bar[stage]);
               stage = (stage + 1) % STAGES;
               ++it;
             }
@@ -453,6 +467,7 @@ OzShape make_oz_shape(int64_t n, int64_t k) {
   s.rows_per_split = rps;
   s.splits = (int)((n + rps - 1) / rps);
   s.units = s.ntiles * s.splits;
+  s.stall = 0;
   return s;
 }
 
@@ -511,14 +526,16 @@ size_t gram_ozaki_workspace(int64_t n, int64_t k) { return carve_oz(nullptr, n, 
 int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int accumulate, double* D, int64_t ldd,
                unsigned* dev_flags, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (k > 65535 || n > ((int64_t)1 << 40)) return DOPINF_E_UNSUPPORTED;
-  const OzShape sh = make_oz_shape(n, k);
+  OzShape sh = make_oz_shape(n, k);
+  sh.stall = (test_stall() & kStallTensorGram) ? 1 : 0;
   if ((int64_t)NDIG * sh.nrb * sh.ncb > (int64_t)INT32_MAX) return DOPINF_E_UNSUPPORTED;
   if (!ws || ws_bytes < gram_ozaki_workspace(n, k) || misaligned(ws)) return DOPINF_E_ARG;
   OzWs w = carve_oz(ws, n, k);
+  DOPINF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(unsigned), st));
   if (dtype == DOPINF_F64)
-    colmax_kernel<double><<<(unsigned)k, 256, 0, st>>>(static_cast<const double*>(Q), n, ldq, w.sexp);
+    colmax_kernel<double><<<(unsigned)k, 256, 0, st>>>(static_cast<const double*>(Q), n, ldq, w.sexp, w.err);
   else
-    colmax_kernel<float><<<(unsigned)k, 256, 0, st>>>(static_cast<const float*>(Q), n, ldq, w.sexp);
+    colmax_kernel<float><<<(unsigned)k, 256, 0, st>>>(static_cast<const float*>(Q), n, ldq, w.sexp, w.err);
   DOPINF_TRY(launch_status());
   {
     // rows split in chunks of 256 threads x 4 rows, enough CTAs for ~32 per SM over all columns
@@ -538,7 +555,6 @@ int gram_ozaki(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int 
   DOPINF_TRY(launch_status());
   CUtensorMap map;
   if (!make_map(&map, w.planes, (int64_t)NDIG * sh.nrb * sh.ncb)) return DOPINF_E_CUDA;
-  DOPINF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(unsigned), st));
   DOPINF_CUDA(cudaFuncSetAttribute(ozaki_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
   {
     int per_sm = 0;  // the kernel needs one resident CTA per SM (registers, shared memory)

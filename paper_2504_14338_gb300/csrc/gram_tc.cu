@@ -65,6 +65,7 @@ struct TcShape {
   int64_t n, nrb;  // nrb: 64-row blocks of the tiled slice planes
   int k, tn, ntiles, splits, units;
   int64_t rows_per_split, chunk_rows;
+  int stall;  // test of the error path: the MMA issuer never releases a stage, so waits expire
 };
 
 // upper-triangle tiles (ta <= tb) of a tn x tn tile grid, row-major
@@ -198,7 +199,7 @@ __global__ void __maxnreg__(96)
             }
             issued = true;
             first = false;
-            mma_commit(&empty_bar[stage]);
+            if (!sh.stall) mma_commit(&empty_bar[stage]);
             stage = (stage + 1) % STAGES;
             ++it;
           }
@@ -298,14 +299,16 @@ __global__ void gram_tc_reduce(const double* __restrict__ part, TcShape sh, int 
 // One TMA box is then one contiguous read.  Rows >= n and columns >= k are written as zeros.
 template <typename T>
 __global__ void split_bf16(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq, __nv_bfloat16* __restrict__ H,
-                           __nv_bfloat16* __restrict__ L, int64_t nrb, int64_t ncb) {
+                           __nv_bfloat16* __restrict__ L, int64_t nrb, int64_t ncb, unsigned* __restrict__ err) {
   const int64_t rows = nrb * BK, cols = ncb * BM;
   const int64_t total = rows * cols;
+  bool bad = false;  // NaN or Inf met: reported through the error word, D is then not valid
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % rows, t = e / rows;
     __nv_bfloat16 h = __float2bfloat16_rn(0.0f), l = h;
     if (i < n && t < k) {
       const T x = Q[i + t * ldq];
+      bad = bad || !isfinite(x);
       if constexpr (sizeof(T) == 8) {
         h = __double2bfloat16(x);
         l = __double2bfloat16(x - (double)__bfloat162float(h));
@@ -318,6 +321,7 @@ __global__ void split_bf16(const T* __restrict__ Q, int64_t n, int64_t k, int64_
     H[off] = h;
     L[off] = l;
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrNonfinite);
 }
 
 TcShape make_shape(int64_t n, int64_t k) {
@@ -349,6 +353,7 @@ TcShape make_shape(int64_t n, int64_t k) {
   if (s.splits < 1) s.splits = 1;
   s.units = s.ntiles * s.splits;
   s.chunk_rows = rps < g_chunk_rows ? rps : g_chunk_rows;
+  s.stall = 0;
   return s;
 }
 
@@ -431,17 +436,18 @@ int gram_tc(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int acc
   if (((n + BK - 1) / BK) * ((k + BM - 1) / BM) > (int64_t)INT32_MAX) return DOPINF_E_UNSUPPORTED;
   if (!ws || ws_bytes < gram_tc_workspace(n, k) || misaligned(ws)) return DOPINF_E_ARG;
   TcWs w = carve_tc(ws, n, k);
-  const TcShape sh = make_shape(n, k);
+  TcShape sh = make_shape(n, k);
+  sh.stall = (test_stall() & kStallTensorGram) ? 1 : 0;
+  DOPINF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(unsigned), st));
   const int64_t total = w.nrb * BK * w.ncb * BM;
   const unsigned sblocks = (unsigned)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
   if (dtype == DOPINF_F64)
-    split_bf16<double><<<sblocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.H, w.L, w.nrb, w.ncb);
+    split_bf16<double><<<sblocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, w.H, w.L, w.nrb, w.ncb, w.err);
   else
-    split_bf16<float><<<sblocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.H, w.L, w.nrb, w.ncb);
+    split_bf16<float><<<sblocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, w.H, w.L, w.nrb, w.ncb, w.err);
   DOPINF_TRY(launch_status());
   CUtensorMap mh, ml;
   if (!make_map(&mh, w.H, w.nrb * w.ncb) || !make_map(&ml, w.L, w.nrb * w.ncb)) return DOPINF_E_CUDA;
-  DOPINF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(unsigned), st));
   DOPINF_CUDA(cudaFuncSetAttribute(gram_bf16x4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
   {
     int per_sm = 0;  // the kernel needs one resident CTA per SM (registers, shared memory)

@@ -57,6 +57,7 @@ constexpr int NW5 = RB5 / 32;
 constexpr int kMaxR5 = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStatusRedo = 4;           // double-word run handed to the FP64 kernel
+constexpr size_t kSmemCeiling = 227 * 1024 - 64;  // dynamic shared memory a CTA may request
 constexpr double kDwRange = 0x1p60;      // magnitude bound of double-word inputs
 
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
@@ -506,7 +507,9 @@ bool cluster_fits(void* fn, int c, int threads = RB5, size_t smem = 0) {
     refused = !ok;
   }
   if (ok && smem > 48 * 1024) {
-    ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    // the function's ceiling, not this launch's size: launches of the same kernel for other r
+    // (other sizes) must stay valid, also inside a graph captured later
+    ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCeiling) == cudaSuccess;
     refused = refused || !ok;
   }
   if (ok) {
@@ -556,7 +559,7 @@ constexpr int RBB = 256;
 constexpr int NWB = RBB / 32;
 constexpr int kMaxRB = 96;       // state entries: three per lane of warp 0
 constexpr int kMaxRBig = 92;     // largest r whose rows fit shared memory in clusters of 16
-constexpr size_t kSmemBig = 227 * 1024 - 64;  // dynamic shared memory per CTA
+constexpr size_t kSmemBig = kSmemCeiling;  // dynamic shared memory per CTA
 constexpr int kMinRowsB = 3, kMaxRowsB = 8;
 
 struct BigLayout {
@@ -965,7 +968,7 @@ int rollout_cols_shape(int r, int* rows, int* cluster) {
   return 0;
 }
 
-int g_arith = DOPINF_ROLLOUT_DW;  // tunable: arithmetic of the learn rollouts
+int g_arith = DOPINF_ROLLOUT_FP64;  // tunable: arithmetic of the learn rollouts (the paper's FP64)
 
 int rollout_set_arith(int a) {
   const int prev = g_arith;

@@ -24,6 +24,7 @@ CENTER, SCALE = 1, 2
 GRAM_FP64, GRAM_BF16X4, GRAM_OZAKI_FP64 = 0, 1, 2
 DISCRETE, CONTINUOUS_RK4 = 0, 1
 ROLLOUT_FP64, ROLLOUT_DW = 1, 2
+TEST_GRID_BARRIER, TEST_TENSOR_GRAM = 1, 2
 
 _c_i64 = ctypes.c_int64
 _c_p = ctypes.c_void_p
@@ -78,6 +79,7 @@ def _load():
         "dopinf_learn_operator_offset": (_c_sz, [_c_i64, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
+        "dopinf_test_expire_waits": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows_large": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_arith": (ctypes.c_int, [ctypes.c_int]),
@@ -212,6 +214,12 @@ def dopinf_gram_async(Q, D, flags, mode=GRAM_FP64, accumulate=False, ws=None, st
 def dopinf_tune_gram_chunk(rows=0):
     """Sets (rows > 0) or queries the FP32 accumulation chunk of the split Gram; returns the previous value."""
     return int(lib.dopinf_tune_gram_chunk(int(rows)))
+
+
+def dopinf_test_expire_waits(which=-1):
+    """Test of the error paths: withholds the signal of the named bounded waits (TEST_GRID_BARRIER,
+    TEST_TENSOR_GRAM) so that they expire; 0 restores; returns the previous value."""
+    return int(lib.dopinf_test_expire_waits(int(which)))
 
 
 def dopinf_tune_rollout_rows_large(rows=0):

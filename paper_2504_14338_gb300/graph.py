@@ -218,7 +218,11 @@ class StreamingPipeline:
         self.count = 0
 
     def submit(self, host_QT):
-        """Queue one step on host_QT (pinned, the shape of the first); returns its index."""
+        """Queue one step on host_QT (pinned, the shape of the first); returns its index.
+
+        The upload from host_QT is asynchronous and may still be running when this returns:
+        the caller must not refill or free host_QT until upload_event(i) has completed (or
+        result(i) has returned); rotate several pinned buffers to keep filling meanwhile."""
         i, b = self.count, self.count % 2
         pg = self.pg[b]
         # the upload into copy b waits for the front graph that last read it (step i - 2)
@@ -238,6 +242,13 @@ class StreamingPipeline:
             self.fetched[b].record(self.stream)
         self.count += 1
         return i
+
+    def upload_event(self, i):
+        """CUDA event recorded when step i's upload has finished (valid until step i + 2 is
+        submitted): host_QT of step i may be reused once it has completed."""
+        if not (self.count - 2 <= i < self.count):
+            raise ValueError("step %d is no longer (or not yet) held" % i)
+        return self.uploaded[i % 2]
 
     def result(self, i):
         """Step i's results on the host (waits for them); valid until step i + 2 is submitted."""

@@ -72,18 +72,16 @@ def test_gram_sampled_entries(run):
 
 
 def test_reduce_full_eigenproblem(run):
+    """The whole 600 x 600 eigenproblem: 1e-10 relative for the eigenvalues above 1e-3 lambda_1
+    and for the Qhat rows whose eigen-gap makes them well determined (eps lambda_1 / gap <=
+    1e-12); the magnitude- or gap-limited ones against the FP64 backward-error bounds."""
+    from test_gpu_parity import assert_eigen_qhat
     w, D, red = run["w"], run["D"].cpu().numpy(), run["red"]
     r = max(w.r_list)
     ref = O.reduce(D, r_fixed=r)
-    lam_ref = ref["lam"]
-    lam = red["eigvals"].cpu().numpy()
-    assert np.all(np.abs(lam - lam_ref[:r]) <= 1e-10 * lam_ref[:r] + 8 * w.k * EPS * lam_ref[0])
-    gaps = np.abs(np.diff(lam_ref))
-    Qh, Qh_ref = red["Qhat"].cpu().numpy(), ref["Qhat"]
-    for j in range(r):
-        gap = min(gaps[j - 1] if j else np.inf, gaps[j])
-        err = np.linalg.norm(Qh[j] - Qh_ref[j]) / np.linalg.norm(Qh_ref[j])
-        assert err <= 1e-10 + 1e3 * w.k * EPS * lam_ref[0] / gap, (j, err)
+    limited = assert_eigen_qhat(red["eigvals"].cpu().numpy(), ref["lam"], red["Qhat"].cpu().numpy(), ref["Qhat"],
+                                w.k, r)
+    assert len(limited["gap_limited_qhat_rows"]) <= r // 2
 
 
 def test_learn_selected_candidate_and_sample(run):

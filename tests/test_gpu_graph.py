@@ -116,3 +116,32 @@ def test_streaming_pipeline_matches_synchronous_calls(dp):
         assert torch.equal(out["O_best"], ref["O_best"].cpu())
     with pytest.raises(ValueError):
         sp.result(0)
+
+
+def test_batched_learn_graph_large_r_of_one_kernel_shape(dp):
+    """Problems with r above 32 whose launches share one kernel (the same rows per CTA) but
+    differ in shared-memory size, the larger first, captured together and replayed twice in
+    both arithmetics: each equal to its own learn call."""
+    from paper_2504_14338_gb300 import synth
+    from paper_2504_14338_gb300.graph import BatchedLearnGraph
+    from test_gpu_parity import _reduced_large
+    Qh = _reduced_large(64)
+    problems = [dict(Qhat=torch.from_numpy(np.ascontiguousarray(Qh[:r].T)).cuda().t(), r_list=[r],
+                     beta1=synth.logspace(-4, 0, 2), beta2=synth.logspace(0, 4, 2)) for r in (60, 48, 36, 52)]
+    prev = dp.dopinf_tune_rollout_arith(0)
+    try:
+        for arith in (dp.ROLLOUT_FP64, dp.ROLLOUT_DW):
+            dp.dopinf_tune_rollout_arith(arith)
+            bg = BatchedLearnGraph(problems, 400, mode=dp.CONTINUOUS_RK4, dt=1e-2).capture()
+            for _ in range(2):
+                bg.replay()
+                torch.cuda.synchronize()
+                for pr, out in zip(problems, bg.out):
+                    ref = dp.dopinf_learn(pr["Qhat"], pr["r_list"], pr["beta1"], pr["beta2"], 400,
+                                          mode=dp.CONTINUOUS_RK4, dt=1e-2)
+                    assert int(out["best"].item()) == ref["best"]
+                    for key in ("train_err", "growth", "status", "steps", "O_best"):
+                        assert torch.equal(out[key], ref[key]), key
+            del bg
+    finally:
+        dp.dopinf_tune_rollout_arith(prev)

@@ -3,8 +3,8 @@
 Tolerances (each derived from the arithmetic, see the comments at each assert):
   transform            bit-exact (same operations, same rounding, fixed summation order)
   Gram (FP64)          |dD| <= 4 sqrt(n) eps max|D|-scale per entry (different summation order)
-  eigenvalues          |dlambda_i| <= 1e-10 lambda_i + 8 k eps lambda_1
-  Qhat (FP64)          1e-10 relative (rows with a healthy eigen-gap)
+  eigenvalues          1e-10 relative where lambda_i >= 1e-3 lambda_1, else 8 k eps lambda_1
+  Qhat (FP64)          1e-10 relative where eps lambda_1 / gap <= 1e-12, else Davis-Kahan
   learn / rollouts     1e-8 relative on well-conditioned candidates (see test)
 """
 import numpy as np
@@ -219,6 +219,40 @@ def _align_signs(U_ref, U):
     return U * s
 
 
+def assert_eigen_qhat(lam, lam_ref, Qh, Qh_ref, k, r):
+    """The FP64 tolerance of the reduce step (1e-10 relative) where the problem allows it.
+
+    Eigenvalues: 1e-10 relative where lambda_i >= 1e-3 lambda_1; below that the eigenvalue
+    is magnitude-limited (any backward-stable solver moves it by about k eps lambda_1, Weyl),
+    and the bound 8 k eps lambda_1 is asserted instead.  Qhat rows: 1e-10 relative where the
+    perturbation estimate eps lambda_1 / gap_i is at most 1e-12 (100 times the rounding of a
+    backward-stable eigensolver); the others are gap-limited and get the Davis-Kahan bound
+    1e3 k eps lambda_1 / gap_i + 1e-10.  Returns the names of the limited modes."""
+    lam_all = np.asarray(lam_ref)
+    lam_ref = lam_all[:r]
+    strict = lam_ref >= 1e-3 * lam_ref[0]
+    rel = np.abs(lam - lam_ref) / np.abs(lam_ref)
+    assert np.all(rel[strict] <= 1e-10), rel[strict].max()
+    assert np.all(np.abs(lam - lam_ref)[~strict] <= 8 * k * EPS * lam_ref[0])
+    limited = {"magnitude_limited_eigenvalues": np.nonzero(~strict)[0].tolist(), "gap_limited_qhat_rows": []}
+    worst = 0.0
+    if Qh_ref is not None:
+        for j in range(r):
+            gap = min(abs(lam_all[j - 1] - lam_all[j]) if j else np.inf,
+                      abs(lam_all[j] - lam_all[j + 1]) if j + 1 < len(lam_all) else np.inf)
+            err = np.linalg.norm(Qh[j] - Qh_ref[j]) / np.linalg.norm(Qh_ref[j])
+            dk = k * EPS * lam_ref[0] / gap
+            if EPS * lam_ref[0] / gap <= 1e-12:
+                assert err <= 1e-10, (j, err)
+                worst = max(worst, err)
+            else:
+                limited["gap_limited_qhat_rows"].append(j)
+                assert err <= 1e3 * dk + 1e-10, (j, err)
+    print("eigenvalue max rel (strict modes) %.2e, Qhat max rel (strict rows) %.2e, limited %s"
+          % (rel[strict].max(), worst, limited))
+    return limited
+
+
 @pytest.mark.parametrize("k,r_cap", [(200, 12), (61, 61), (3, 2), (1, 1), (130, 40)])
 def test_reduce_vs_oracle(dp, k, r_cap):
     rng = np.random.default_rng(k)
@@ -228,28 +262,20 @@ def test_reduce_vs_oracle(dp, k, r_cap):
     res = dp.dopinf_reduce(Dd, r_cap=r_cap, r_fixed=r_cap)
     lam_ref, U_ref = O.eig_desc(D)
     lam = res["eigvals"].cpu().numpy()
-    tol = 1e-10 * np.abs(lam_ref[:r_cap]) + 8 * k * EPS * lam_ref[0]
-    assert np.all(np.abs(lam - lam_ref[:r_cap]) <= tol)
-    # eigenvectors: compare where the gap to the neighbours makes them well determined
-    gaps = np.abs(np.diff(lam_ref))
+    Qh = res["Qhat"].cpu().numpy()
+    Qh_ref = O.projection(D, U_ref, lam_ref, r_cap)[1] if lam_ref[r_cap - 1] > 0 else None
+    # with k = r_cap the next eigenvalue is absent: its gap is the distance to the end
+    lam_full = np.concatenate([lam_ref, [0.0]]) if r_cap == k else lam_ref
+    assert_eigen_qhat(lam, lam_full, Qh, Qh_ref, k, r_cap)
+    # eigenvectors (T_r scaled back): the same gap rule
+    gaps = np.abs(np.diff(lam_full))
     Tr = res["Tr"].cpu().numpy()
     U = Tr * np.sqrt(np.maximum(lam, 1e-300))
     for j in range(r_cap):
-        gap = min(gaps[j - 1] if j > 0 else np.inf, gaps[j] if j < k - 1 else np.inf)
-        if gap < 1e-6 * lam_ref[0]:
-            continue
-        bound = 1e3 * k * EPS * lam_ref[0] / gap + 1e-12
+        gap = min(gaps[j - 1] if j > 0 else np.inf, gaps[j] if j < len(gaps) else np.inf)
+        dk = k * EPS * lam_ref[0] / gap
+        bound = 1e-10 if EPS * lam_ref[0] / gap <= 1e-12 else 1e3 * dk + 1e-12
         assert np.linalg.norm(U[:, j] - U_ref[:, j]) <= bound, j
-    # Qhat = T^T D, rows compared where well determined
-    Qh = res["Qhat"].cpu().numpy()
-    Tr_ref, Qh_ref = O.projection(D, U_ref, lam_ref, r_cap) if lam_ref[r_cap - 1] > 0 else (None, None)
-    if Qh_ref is not None:
-        for j in range(r_cap):
-            gap = min(gaps[j - 1] if j > 0 else np.inf, gaps[j] if j < k - 1 else np.inf)
-            if gap < 1e-6 * lam_ref[0]:
-                continue
-            err = np.linalg.norm(Qh[j] - Qh_ref[j]) / np.linalg.norm(Qh_ref[j])
-            assert err <= 1e3 * k * EPS * lam_ref[0] / gap + 1e-10, (j, err)
 
 
 @pytest.mark.parametrize("s", [-300, 300])
@@ -321,6 +347,7 @@ def test_reduce_energy_rank_and_pipeline_qhat(dp):
     rel = np.linalg.norm(Qh - Qh_ref, axis=1) / np.linalg.norm(Qh_ref, axis=1)
     print("Qhat row rel err", rel)
     assert np.all(rel < 1e-10)
+    assert_eigen_qhat(res["eigvals"].cpu().numpy()[:r], ref["lam"], Qh, Qh_ref, D.shape[0], r)
     # the target is out of reach of r_cap = 1 eigenpairs: the energy rule reports it
     with pytest.raises(dp.DopinfError) as ei:
         dp.dopinf_reduce(torch.from_numpy(D).cuda(), r_cap=1, energy_target=0.9996)
