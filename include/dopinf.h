@@ -271,7 +271,7 @@ int dopinf_tune_reduce_coop(int on);
  * Workspace: dopinf_learn_workspace(...) bytes.
  * ------------------------------------------------------------------------------------ */
 /* Tuning of the rollouts of r <= 32 (dopinf_learn, dopinf_learn_async, dopinf_rollout): rows
- * of O per CTA, 1, 2 or 4 (default 4; raised where the cluster of ceil(r / rows) CTAs would
+ * of O per CTA, 1, 2, 4 or 8 (default 4; raised where the cluster of ceil(r / rows) CTAs would
  * exceed 16 or cannot be resident); other values only query.  Returns the previous value.
  * Process-wide.  The results do not depend on it. */
 int dopinf_tune_rollout_rows(int rows);

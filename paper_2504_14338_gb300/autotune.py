@@ -3,7 +3,7 @@
 Two knobs decide how the work is laid out on the GPU without changing a single bit of the
 results (both choices are exercised by the GPU tests):
 
-* how many operator rows each CTA of a rollout cluster owns (1, 2 or 4 for r <= 32, 3 to 8 for
+* how many operator rows each CTA of a rollout cluster owns (1, 2, 4 or 8 for r <= 32, 3 to 8 for
   r above 32, so ceil(r / rows) CTAs per candidate): large clusters shorten each candidate's
   chain of evaluations, small ones leave more of the GPU's issue slots to the other candidates;
 * the Householder tridiagonalisation as one cooperative launch (a grid barrier per column) or
@@ -34,7 +34,7 @@ def _key(kind, *parts):
     return (kind, torch.cuda.get_device_name(), *parts)
 
 
-def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, rows=(1, 2, 4),
+def tune_learn(Qhat, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0, rows=(1, 2, 4, 8),
                rows_large=(3, 4, 5, 6, 8), reps=3, ws=None, timer=None):
     """Time the rollouts of this grid search for each launch shape; set and return the best.
 

@@ -129,6 +129,7 @@ struct RolloutCand {
   int cand;             // index into the per-candidate outputs
   const double* mu;     // temporal mean of the reference data (r), metrics runs only
   const double* denom;  // max_{t<k,i} |qhat - mu|, metrics runs only
+  const double* inv_den;  // 1 / sum_i qhat_{i,t}^2 for t < k, metrics runs only
 };
 
 struct RolloutBatch {
@@ -161,7 +162,7 @@ struct RolloutBatch {
 
 // Rollouts (rollout.cu).  Column-owned kernel for r <= 32: whether r is supported, the rows per
 // CTA and cluster size a launch for r would use (0 if none fits), the process-wide preferred
-// rows per CTA (1, 2, 4; other values only query; returns the previous value), and the launch
+// rows per CTA (1, 2, 4, 8; other values only query; returns the previous value), and the launch
 // of candidates [cand0, cand0 + n) of one r (chained: programmatic dependent launch behind the
 // previous rollout launch on the stream, which it completes after).  Shared-memory kernel for
 // 32 < r <= 92: the same, with preferred rows per CTA 3..8.

@@ -66,8 +66,17 @@ __global__ void __launch_bounds__(LB) build_features(const double* __restrict__ 
   }
 }
 
+// Per r: the temporal mean mu of the reference data, denom = max_{t<k,i} |qhat - mu| (the
+// growth ratio's denominator), and 1 / ||qhat_t||^2 for every t < k (the training error's
+// denominators, so that the rollouts multiply instead of dividing on their critical path).
 __global__ void __launch_bounds__(LB) train_stats(const double* __restrict__ Qhat, int64_t ldqh, int r, int64_t k,
-                                                  double* __restrict__ mu, double* __restrict__ denom) {
+                                                  double* __restrict__ mu, double* __restrict__ denom,
+                                                  double* __restrict__ inv_den) {
+  for (int64_t t = threadIdx.x; t < k; t += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < r; ++i) s += Qhat[i + t * ldqh] * Qhat[i + t * ldqh];
+    inv_den[t] = 1.0 / s;
+  }
   __shared__ double sh[LB];
   double dev = 0.0;
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
@@ -101,10 +110,11 @@ struct LearnWs {
   SchurUnit* units;
   SchurCand* cands;
   RolloutCand* roll;
-  double *mu, *denom, *Dh, *Y;
+  double *mu, *denom, *invden, *Dh, *Y;
   double *G[kMaxR], *B[kMaxR], *E[kMaxR], *S[kMaxR], *O[kMaxR];
   size_t O_off[kMaxR];  // byte offset of O[i] in the workspace
   int r_stride;  // largest r of the list: stride of the per-r vectors (mu)
+  int64_t k_stride;  // snapshots: stride of the per-r training-error denominators
   int *best, *unit_fail;
   void* tn;
   size_t tn_bytes, used;
@@ -127,6 +137,8 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1,
   w.unit_fail = c.take<int>((size_t)n_r * n_b2);
   w.mu = c.take<double>((size_t)n_r * r_max);
   w.denom = c.take<double>(n_r);
+  w.k_stride = K + 1;
+  w.invden = c.take<double>((size_t)n_r * (K + 1));
   w.best = c.take<int>(1);
   w.Dh = c.take<double>((size_t)K * d_max);
   w.Y = c.take<double>((size_t)K * r_max);
@@ -232,6 +244,7 @@ __global__ void build_tables(const LearnGrid g) {
     R.cand = c;
     R.mu = g.w.mu + (size_t)ir * g.w.r_stride;
     R.denom = g.w.denom + ir;
+    R.inv_den = g.w.invden + (size_t)ir * g.w.k_stride;
     g.w.roll[c] = R;
   }
 }
@@ -324,7 +337,8 @@ int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
     DOPINF_TRY(launch_status());
     DOPINF_TRY(tn_product(w.Dh, K, w.Dh, K, DOPINF_F64, K, d, d, 1, 0, w.G[ir], d, w.tn, w.tn_bytes, st));
     DOPINF_TRY(tn_product(w.Dh, K, w.Y, K, DOPINF_F64, K, d, r, 0, 0, w.B[ir], d, w.tn, w.tn_bytes, st));
-    train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * w.r_stride, w.denom + ir);
+    train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * w.r_stride, w.denom + ir,
+                                  w.invden + (size_t)ir * w.k_stride);
     DOPINF_TRY(launch_status());
   }
   if (ev) DOPINF_CUDA(cudaEventRecord(ev[1], st));

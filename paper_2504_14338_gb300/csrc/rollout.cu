@@ -147,7 +147,7 @@ __device__ __forceinline__ V warp_rows_sum(const V (&acc)[RC], int lane) {
 }
 
 template <int NT, int RC, bool DW>
-__global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBatch bt, int cand0) {
+__global__ void __launch_bounds__(RB5, RC == 8 ? 3 : (DW ? 5 : 6)) rollout_cols_kernel(RolloutBatch bt, int cand0) {
   using Part = typename std::conditional<DW, csum, double>::type;
   __shared__ double xs[kMaxR5 + 2];    // FP64 stage state; xs[r] = 1, xs[r + 1] = 0
   __shared__ float xh[kMaxR5 + 2];     // double-word stage state (high, low words)
@@ -252,14 +252,16 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
     const double dt = bt.dt, h2 = 0.5 * dt, h6 = dt / 6.0;
     const dw dtw = dw_of(dt), h2w = dw_of(h2), h6w = dw_of(h6);
     const double denom = bt.metrics ? *cd.denom : 1.0;
-    // metrics as in the row-split kernel: max of num/den (one square root at the end), the
-    // largest |q - mu| as an integer maximum of bit patterns.  FP64: growth decided by a band
+    // metrics: the largest num/den (one square root at the end), the largest |q - mu| as an
+    // integer maximum of bit patterns.  FP64: growth decided by a band
     // of 2^-40 around max_growth * denom with the division only inside it.  Double-word: the
     // state differs from the FP64 one by rounding, so a growth inside a band of 2^-20 around
     // the threshold hands the candidate to the FP64 kernel instead of deciding it here; since
     // the growth maximum only rises, a candidate stopped for growth above the band stops at
     // the same step in FP64, and a valid one stays below the threshold there too.
-    double rat = 0.0;
+    // the training error as the largest num_t / ||qhat_t||^2, with the reciprocals formed once
+    // per r, held as the bits of a non-negative double (an integer maximum)
+    unsigned long long ratb = 0ull;
     unsigned long long gnumb = 0ull;
     const double thr = bt.max_growth * denom;
     const bool band_ok = denom > 0.0 && isfinite(thr) && thr > 0.0;
@@ -269,19 +271,18 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
     const unsigned long long band_hi =
         band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + bw)) : ~0ull;
     int st = 0;
+    double icur = (lane == 0 && bt.metrics && bt.k > 0) ? cd.inv_den[0] : 0.0;
 
-    // metrics of state t (warp 0); lane 0 publishes the stop decision
+    // metrics of state t (warp 0); lane 0 publishes the stop decision.  The finiteness test and
+    // the maxima are integer operations on the encodings (FP64 issue is scarce on this path).
     auto check = [&](int64_t t) {
       if constexpr (DW) qv = dw_value(qw);
-      bool fin = !own || isfinite(qv);
+      bool fin = !own || ((((unsigned long long)__double_as_longlong(qv)) >> 52) & 0x7ffull) != 0x7ffull;
       unsigned long long devb = 0ull;
-      double num = 0.0, den = 0.0;
+      double num = 0.0;
       if (own && bt.metrics) {
-        devb = (unsigned long long)__double_as_longlong(fabs(qv - mu));
-        if (t < bt.k) {
-          num = (qv - hcur) * (qv - hcur);
-          den = hcur * hcur;
-        }
+        devb = (unsigned long long)__double_as_longlong(qv - mu) & 0x7fffffffffffffffull;
+        if (t < bt.k) num = (qv - hcur) * (qv - hcur);
       }
       if (own && bt.traj && rank == 0) bt.traj_out[t * r + lane] = qv;
       fin = __all_sync(kFull, fin);
@@ -293,14 +294,15 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
           devb = ob > devb ? ob : devb;
         }
         if (t < bt.k) {
-          const double nd[2] = {num, den};
-          const double v = warp_rows_sum<2>(nd, lane);  // lanes < 16: num, lanes >= 16: den
-          num = v;
-          den = __shfl_sync(kFull, v, 16);
+          const double v1[1] = {num};
+          num = warp_rows_sum<1>(v1, lane);
         }
         if (lane == 0 && fin) {
           gnumb = devb > gnumb ? devb : gnumb;
-          if (t < bt.k) rat = fmax(rat, num / den);
+          if (t < bt.k) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(num * icur);
+            ratb = b > ratb ? b : ratb;
+          }
         }
       }
       if (lane == 0) {
@@ -389,8 +391,9 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
     for (int64_t t = 0;; ++t) {
       t_end = t;
       // the reference state of step t + 1 for the training error, fetched a step early
-      double hnext = 0.0;
+      double hnext = 0.0, inext = 0.0;
       if (own && bt.metrics && t + 1 < bt.k) hnext = bt.Qhat[lane + (t + 1) * bt.ldqh];
+      if (lane == 0 && warp == 0 && bt.metrics && t + 1 < bt.k) inext = cd.inv_den[t + 1];
       const Part k1 = eval(true, t);
       if (bt.mode == DOPINF_DISCRETE) {
         if constexpr (DW) {
@@ -444,6 +447,7 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
         __syncthreads();
       }
       hcur = hnext;
+      icur = inext;
     }
     cl.sync();  // no CTA leaves while a peer may still read its partial sums
     if (rank == 0 && tid == 0) {
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(RB5, DW ? 5 : 6) rollout_cols_kernel(RolloutBa
         if (bt.steps) bt.steps[cd.cand] = t_end;
         if (bt.metrics) {
           bt.status[cd.cand] = st;
-          bt.train_err[cd.cand] = st == 0 ? sqrt(rat) : INFINITY;
+          bt.train_err[cd.cand] = st == 0 ? sqrt(__longlong_as_double((long long)ratb)) : INFINITY;
           bt.growth[cd.cand] = st == 2 ? INFINITY : __longlong_as_double((long long)gnumb) / denom;
         }
         if (bt.traj && bt.finite) *bt.finite = st == 2 ? 0 : 1;
@@ -472,19 +476,19 @@ void* cols_kernel_ptr() {
 
 void* cols_kernel(int nt, int rc, bool dw) {
   using F = void* (*)();
-  static const F tab[2][5][3] = {
-      {{cols_kernel_ptr<1, 1, false>, cols_kernel_ptr<1, 2, false>, cols_kernel_ptr<1, 4, false>},
-       {cols_kernel_ptr<2, 1, false>, cols_kernel_ptr<2, 2, false>, cols_kernel_ptr<2, 4, false>},
-       {cols_kernel_ptr<3, 1, false>, cols_kernel_ptr<3, 2, false>, cols_kernel_ptr<3, 4, false>},
-       {cols_kernel_ptr<4, 1, false>, cols_kernel_ptr<4, 2, false>, cols_kernel_ptr<4, 4, false>},
-       {cols_kernel_ptr<5, 1, false>, cols_kernel_ptr<5, 2, false>, cols_kernel_ptr<5, 4, false>}},
-      {{cols_kernel_ptr<1, 1, true>, cols_kernel_ptr<1, 2, true>, cols_kernel_ptr<1, 4, true>},
-       {cols_kernel_ptr<2, 1, true>, cols_kernel_ptr<2, 2, true>, cols_kernel_ptr<2, 4, true>},
-       {cols_kernel_ptr<3, 1, true>, cols_kernel_ptr<3, 2, true>, cols_kernel_ptr<3, 4, true>},
-       {cols_kernel_ptr<4, 1, true>, cols_kernel_ptr<4, 2, true>, cols_kernel_ptr<4, 4, true>},
-       {cols_kernel_ptr<5, 1, true>, cols_kernel_ptr<5, 2, true>, cols_kernel_ptr<5, 4, true>}},
+  static const F tab[2][5][4] = {
+      {{cols_kernel_ptr<1, 1, false>, cols_kernel_ptr<1, 2, false>, cols_kernel_ptr<1, 4, false>, cols_kernel_ptr<1, 8, false>},
+       {cols_kernel_ptr<2, 1, false>, cols_kernel_ptr<2, 2, false>, cols_kernel_ptr<2, 4, false>, cols_kernel_ptr<2, 8, false>},
+       {cols_kernel_ptr<3, 1, false>, cols_kernel_ptr<3, 2, false>, cols_kernel_ptr<3, 4, false>, cols_kernel_ptr<3, 8, false>},
+       {cols_kernel_ptr<4, 1, false>, cols_kernel_ptr<4, 2, false>, cols_kernel_ptr<4, 4, false>, cols_kernel_ptr<4, 8, false>},
+       {cols_kernel_ptr<5, 1, false>, cols_kernel_ptr<5, 2, false>, cols_kernel_ptr<5, 4, false>, cols_kernel_ptr<5, 8, false>}},
+      {{cols_kernel_ptr<1, 1, true>, cols_kernel_ptr<1, 2, true>, cols_kernel_ptr<1, 4, true>, cols_kernel_ptr<1, 8, true>},
+       {cols_kernel_ptr<2, 1, true>, cols_kernel_ptr<2, 2, true>, cols_kernel_ptr<2, 4, true>, cols_kernel_ptr<2, 8, true>},
+       {cols_kernel_ptr<3, 1, true>, cols_kernel_ptr<3, 2, true>, cols_kernel_ptr<3, 4, true>, cols_kernel_ptr<3, 8, true>},
+       {cols_kernel_ptr<4, 1, true>, cols_kernel_ptr<4, 2, true>, cols_kernel_ptr<4, 4, true>, cols_kernel_ptr<4, 8, true>},
+       {cols_kernel_ptr<5, 1, true>, cols_kernel_ptr<5, 2, true>, cols_kernel_ptr<5, 4, true>, cols_kernel_ptr<5, 8, true>}},
   };
-  const int ri = rc == 1 ? 0 : rc == 2 ? 1 : rc == 4 ? 2 : -1;
+  const int ri = rc == 1 ? 0 : rc == 2 ? 1 : rc == 4 ? 2 : rc == 8 ? 3 : -1;
   if (nt < 1 || nt > 5 || ri < 0) return nullptr;
   return tab[dw ? 1 : 0][nt - 1][ri]();
 }
@@ -538,7 +542,8 @@ bool cluster_fits(void* fn, int c, int threads = RB5, size_t smem = 0) {
 
 // ---------------------------------------------------------------------------------------
 // Column-owned rollouts for 32 < r <= 92 (the batched-learn workloads reach r = 80,
-// d = 3321; at r = 92 six rows of d = 4371 fill the 227 KB of shared memory).  The operator no longer fits registers, so each CTA keeps its RC rows of O in
+// d = 3321; at r = 92 six rows of d = 4371 fill the 227 KB of shared memory).  The operator no
+// longer fits registers, so each CTA keeps its RC rows of O in
 // shared memory (row rho at rho * d: a warp reads 32 consecutive entries of a row, free of
 // bank conflicts), and 256 threads walk the d columns: thread tid forms phi_a for the
 // columns a = tid + 256 j from the stage state and adds O[i][a] phi_a into its RC row sums.
@@ -688,7 +693,7 @@ __global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, in
   const double dt = bt.dt, h2 = 0.5 * dt, h6 = dt / 6.0;
   const dw dtw = dw_of(dt), h2w = dw_of(h2), h6w = dw_of(h6);
   const double denom = bt.metrics ? *cd.denom : 1.0;
-  double rat = 0.0;
+  unsigned long long ratb = 0ull;  // largest num_t / ||qhat_t||^2 (bits of a non-negative double)
   unsigned long long gnumb = 0ull;
   const double thr = bt.max_growth * denom;
   const bool band_ok = denom > 0.0 && isfinite(thr) && thr > 0.0;
@@ -696,25 +701,23 @@ __global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, in
   const unsigned long long band_lo = band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 - bw)) : 0ull;
   const unsigned long long band_hi = band_ok ? (unsigned long long)__double_as_longlong(thr * (1.0 + bw)) : ~0ull;
   int st = 0;
+  double icur = (warp == 0 && lane == 0 && bt.metrics && bt.k > 0) ? cd.inv_den[0] : 0.0;
 
   // metrics of state t (warp 0, the same values in every CTA); lane 0 publishes the decision
   auto check = [&](int64_t t) {
     bool fin = true;
     unsigned long long devb = 0ull;
-    double num = 0.0, den = 0.0;
+    double num = 0.0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int i = lane + 32 * j;
       if (i >= r) continue;
       if constexpr (DW) qv[j] = dw_value(qw[j]);
-      fin = fin && isfinite(qv[j]);
+      fin = fin && ((((unsigned long long)__double_as_longlong(qv[j])) >> 52) & 0x7ffull) != 0x7ffull;
       if (bt.metrics) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(qv[j] - mu[j]));
+        const unsigned long long b = (unsigned long long)__double_as_longlong(qv[j] - mu[j]) & 0x7fffffffffffffffull;
         devb = b > devb ? b : devb;
-        if (t < bt.k) {
-          num += (qv[j] - hcur[j]) * (qv[j] - hcur[j]);
-          den += hcur[j] * hcur[j];
-        }
+        if (t < bt.k) num += (qv[j] - hcur[j]) * (qv[j] - hcur[j]);
       }
       if (bt.traj && rank == 0) bt.traj_out[t * r + i] = qv[j];
     }
@@ -726,14 +729,15 @@ __global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, in
         devb = ob > devb ? ob : devb;
       }
       if (t < bt.k) {
-        const double nd[2] = {num, den};
-        const double v = warp_rows_sum<2>(nd, lane);  // lanes < 16: num, lanes >= 16: den
-        num = v;
-        den = __shfl_sync(kFull, v, 16);
+        const double v1[1] = {num};
+        num = warp_rows_sum<1>(v1, lane);
       }
       if (lane == 0 && fin) {
         gnumb = devb > gnumb ? devb : gnumb;
-        if (t < bt.k) rat = fmax(rat, num / den);
+        if (t < bt.k) {
+          const unsigned long long b = (unsigned long long)__double_as_longlong(num * icur);
+          ratb = b > ratb ? b : ratb;
+        }
       }
     }
     if (lane == 0) {
@@ -825,6 +829,7 @@ __global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, in
       const int i = lane + 32 * j;
       hnext[j] = (warp == 0 && i < r && bt.metrics && t + 1 < bt.k) ? bt.Qhat[i + (t + 1) * bt.ldqh] : 0.0;
     }
+    const double inext = (warp == 0 && lane == 0 && bt.metrics && t + 1 < bt.k) ? cd.inv_den[t + 1] : 0.0;
     int b = eval(true, t);
     if (bt.mode == DOPINF_DISCRETE) {
       if (warp == 0) {
@@ -908,6 +913,7 @@ __global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, in
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) hcur[j] = hnext[j];
+    icur = inext;
   }
   cl.sync();  // no CTA leaves while a peer may still store into its shared memory
   if (rank == 0 && tid == 0) {
@@ -917,7 +923,7 @@ __global__ void __launch_bounds__(RBB, 2) rollout_big_kernel(RolloutBatch bt, in
       if (bt.steps) bt.steps[cd.cand] = t_end;
       if (bt.metrics) {
         bt.status[cd.cand] = st;
-        bt.train_err[cd.cand] = st == 0 ? sqrt(rat) : INFINITY;
+        bt.train_err[cd.cand] = st == 0 ? sqrt(__longlong_as_double((long long)ratb)) : INFINITY;
         bt.growth[cd.cand] = st == 2 ? INFINITY : __longlong_as_double((long long)gnumb) / denom;
       }
       if (bt.traj && bt.finite) *bt.finite = st == 2 ? 0 : 1;
@@ -954,7 +960,7 @@ bool rollout_cols_supported(int r) { return r >= 1 && r <= kMaxR5 && (dim_d(r) +
 int rollout_cols_shape(int r, int* rows, int* cluster) {
   if (!rollout_cols_supported(r)) return 0;
   const int nt = (dim_d(r) + RB5 - 1) / RB5;
-  for (int rc = g_rows_want; rc <= 4; rc *= 2) {
+  for (int rc = g_rows_want; rc <= 8; rc *= 2) {
     const int c = (r + rc - 1) / rc;
     if (c > 16) continue;
     void* f64 = cols_kernel(nt, rc, false);
@@ -980,7 +986,7 @@ int rollout_arith() { return g_arith; }
 
 int rollout_set_rows(int rc) {
   const int prev = g_rows_want;
-  if (rc == 1 || rc == 2 || rc == 4) g_rows_want = rc;
+  if (rc == 1 || rc == 2 || rc == 4 || rc == 8) g_rows_want = rc;
   return prev;
 }
 

@@ -235,7 +235,7 @@ def dopinf_tune_rollout_arith(arith=0):
 
 
 def dopinf_tune_rollout_rows(rows=0):
-    """Sets (1, 2, 4) or queries the operator rows per CTA of the rollouts of r <= 32 (the
+    """Sets (1, 2, 4, 8) or queries the operator rows per CTA of the rollouts of r <= 32 (the
     cluster of one candidate has ceil(r / rows) CTAs, at most 16); returns the previous value."""
     return int(lib.dopinf_tune_rollout_rows(int(rows)))
 
