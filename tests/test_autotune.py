@@ -38,9 +38,9 @@ def test_injected_timings_drive_the_choice(monkeypatch):
         shape = (30, 600)
 
     # r <= 32: rows per CTA of the column-owned rollouts
-    small = {1: 9.0, 2: 4.0, 4: 6.5}
+    small = {1: 9.0, 2: 4.0, 4: 6.5, 8: 7.5}
     out = autotune.tune_learn(Q(), [10, 20, 30], [1] * 8, [1] * 8, 5000, timer=lambda k, c: small[c])
-    assert out["best"] == 2 and out["rollout_ms"][2] == 4.0 and set(out["rollout_ms"]) == {1, 2, 4}
+    assert out["best"] == 2 and out["rollout_ms"][2] == 4.0 and set(out["rollout_ms"]) == {1, 2, 4, 8}
     assert out["knob"] == "rollout rows per CTA"
     assert set_calls[-1] == ("rows", 2)  # the winner is set process-wide
     assert len(out["knobs"]) == 1
