@@ -7,7 +7,7 @@ or helpers with the CUDA library; the only thing both sides consume is the seede
 input generator module, which contains none of the method's arithmetic.
 
 Every function follows one step of the paper (Section 3.3 Step II, Section 3.4 Step III,
-Section 3.5 Step IV) in the paper's order and notation.  Library primitives (numpy
+Section 3.5 Step IV, Section 3.6 Step V) in the paper's order and notation.  Library primitives (numpy
 matmul, ``np.linalg.eigh``, ``np.linalg.solve``, ``np.linalg.cholesky``) serve as steps;
 there is no blocking or fusion beyond what the paper's definitions state.
 
@@ -39,7 +39,7 @@ __all__ = [
     "transform", "gram", "eig_desc", "energy_rank", "projection", "qhat_sq",
     "data_matrix", "normal_equations", "regulariser", "solve_cholesky", "solve_lu",
     "split_operators", "rom_step_discrete", "rom_rhs", "rk4_step", "rollout",
-    "train_error", "growth_ratio", "learn", "reduce", "pipeline",
+    "train_error", "growth_ratio", "learn", "reduce", "pipeline", "pod_basis_rows", "lift",
 ]
 
 NONFINITE = 1
@@ -334,6 +334,31 @@ def learn(Qhat, r_list, beta1s, beta2s, n_steps, mode="discrete", dt=1.0,
         out.update(r=r, beta1=b1, beta2=b2, O=ops[best],
                    Qtilde=rollout(ops[best], r, Qhat[:r, 0], n_steps, mode, dt))
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Step V (Section 3.6): the reduced solution back in the original coordinates.
+# --------------------------------------------------------------------------------------
+def pod_basis_rows(Q, Tr, rows):
+    """Rows of the rank-r POD basis V_r = Q T_r (eq. MoS_POD_basis), at the given row indices
+    of the transformed snapshot matrix Q (n x k)."""
+    Q64 = np.asarray(Q, dtype=np.float64)
+    return Q64[np.asarray(rows, dtype=np.int64), :] @ np.asarray(Tr, dtype=np.float64)
+
+
+def lift(Q, Tr, Qtilde, rows, row_mean=None, var_scale=None, var_row_offsets=None):
+    """Step V: the reduced solution Qtilde (r x n_t, column t = state t) lifted at the given rows:
+    V_r[rows] Qtilde, then the inverse of Step II's transform, x = (scale of the row's variable)
+    * y + (the row's temporal mean); either part is skipped when its argument is None.
+    Returns (len(rows), n_t)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    Y = pod_basis_rows(Q, Tr, rows) @ np.asarray(Qtilde, dtype=np.float64)
+    if var_scale is not None:
+        var = np.searchsorted(np.asarray(var_row_offsets), rows, side="right") - 1
+        Y = Y * np.asarray(var_scale, dtype=np.float64)[var][:, None]
+    if row_mean is not None:
+        Y = Y + np.asarray(row_mean, dtype=np.float64)[rows][:, None]
+    return Y
 
 
 def pipeline(Q, var_row_offsets, r_list=None, beta1s=(), beta2s=(), n_steps=0,

@@ -336,3 +336,49 @@ def test_grid_matches_printed_optimum():
         inside = [i for i, v in enumerate(grid) if val <= v < val + unit]
         assert inside == [idx]
     assert B1[0] == 1e-10 and B1[-1] == 1.0 and B2[0] == 1e-4 and B2[-1] == 1e4
+
+
+# ----------------------------------------------------------------------------- Step V
+def test_lift_recovers_the_snapshots_with_every_mode():
+    """With r equal to the rank of the centred data, V_r V_r^T is the projector onto its range:
+    lifting the reduced coordinates of the training data (Qhat = V_r^T Q) returns the
+    transformed snapshots, and undoing the transform returns the raw snapshots."""
+    rng = np.random.default_rng(11)
+    n, k, rank = 400, 30, 7
+    Q = rng.standard_normal((n, rank)) @ rng.standard_normal((rank, k)) + rng.standard_normal((n, 1)) * 3.0
+    Q[200:] *= 50.0
+    offs = [0, 200, 400]
+    Qt, mean, scale, _ = O.transform(Q, offs)
+    # the numerical rank of the centred, scaled data (at most 7: centring may remove a direction)
+    lam = O.reduce(O.gram(Qt), r_fixed=1)["lam"]
+    r = int(np.sum(lam > 1e-10 * lam[0]))
+    red = O.reduce(O.gram(Qt), r_fixed=r)
+    rows = np.array([0, 5, 199, 200, 333, 399])
+    X = O.lift(Qt, red["Tr"], red["Qhat"], rows, mean, scale, offs)
+    assert np.allclose(X, Q[rows], rtol=1e-10, atol=1e-10 * np.abs(Q).max())
+    Y = O.lift(Qt, red["Tr"], red["Qhat"], rows)
+    assert np.allclose(Y, Qt[rows], atol=1e-12)
+
+
+def test_lift_basis_equals_left_singular_vectors():
+    """V_r = Q T_r are the leading left singular vectors of Q (sign-aligned), computed here by
+    numpy's SVD: the lifted rows equal U_r[rows] Sigma_r W_r^T restricted to the rows."""
+    rng = np.random.default_rng(12)
+    Q = rng.standard_normal((120, 15)) @ np.diag(0.7 ** np.arange(15))
+    red = O.reduce(O.gram(Q), r_fixed=5)
+    U, S, Wt = np.linalg.svd(Q, full_matrices=False)
+    V = O.pod_basis_rows(Q, red["Tr"], np.arange(120))
+    s = np.sign(np.sum(U[:, :5] * V, axis=0))
+    assert np.allclose(V, U[:, :5] * s, atol=1e-12)
+    Qtilde = rng.standard_normal((5, 9))
+    rows = [3, 77, 119]
+    assert np.allclose(O.lift(Q, red["Tr"], Qtilde, rows), (U[:, :5] * s)[rows] @ Qtilde, atol=1e-12)
+
+
+def test_lift_inverse_transform_by_hand():
+    """The inverse transform on a hand input: y * scale + mean per row, with the row's variable."""
+    Q = np.eye(3)
+    Tr = np.eye(3)[:, :2]
+    Qtilde = np.array([[1.0, 2.0], [3.0, 4.0]])
+    X = O.lift(Q, Tr, Qtilde, [0, 1, 2], np.array([10.0, 20.0, 30.0]), np.array([2.0, 5.0]), [0, 2, 3])
+    assert X.tolist() == [[12.0, 14.0], [26.0, 28.0], [30.0, 30.0]]
