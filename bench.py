@@ -410,6 +410,38 @@ def paper_shape_measure(dp, synth, dev, reps=3):
                                                       "HDF5 loading included (Section 4)"}}
 
 
+def lift_measure(dp, Q, offs, mean, scale, red, res, w, mode, reps=3):
+    """Step V on the benchmark workload: the selected ROM's rollout lifted at three probe rows
+    of every variable (the paper's use), and the whole field at ten time instants; CUDA-event
+    times and the bytes of the snapshot matrix each lift reads."""
+    import torch
+    if res.get("r") is None:
+        return None
+    r = res["r"]
+    traj, _ = dp.dopinf_rollout(res["O"], red["Qhat"][:r, 0].contiguous(), w.n_steps, mode=mode, dt=w.snap_dt)
+    Tr = red["Tr"][:, :r]
+    probes = torch.tensor([v * w.n_per_var + p for v in range(w.n_vars) for p in (1234, w.n_per_var // 2,
+                                                                                   w.n_per_var - 7)],
+                          dtype=torch.int64, device=Q.device)
+    times = torch.linspace(0, w.n_steps - 1, 10).round().long()
+    field_qt = traj[times.to(traj.device)].t()   # r x 10, column-major (rows of traj are states)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, kw, qt in (("probes", dict(rows=probes), traj.t()), ("field_10_instants", {}, field_qt)):
+        best = None
+        for _ in range(reps + 1):
+            a, b = _events(2)
+            a.record(stream)
+            dp.dopinf_lift(Q, Tr, qt, row_mean=mean, var_scale=scale, var_row_offsets=offs, **kw)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+        n_rows = probes.numel() if name == "probes" else Q.shape[0]
+        out[name] = {"ms": best, "rows": n_rows, "times": qt.shape[1],
+                     "fp64_gflops": 2.0 * n_rows * (Q.shape[1] * r + r * qt.shape[1]) / best / 1e6}
+    return out
+
+
 def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16):
     """The batched learn configuration on a stated subset: n_problems of its 512 problems (r drawn
     from U{10..80} with a fixed seed; reduced data of k = 1500 from step-flow-style generators,
@@ -577,7 +609,7 @@ def main():
     def step(record=False):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         e[0].record(stream)
-        dp.dopinf_transform(Q, offs, ws=ws)
+        last["mean"], last["scale"], _ = dp.dopinf_transform(Q, offs, ws=ws)
         e[1].record(stream)
         D = dp.dopinf_gram(Q, mode=pipe_mode, ws=ws)
         last["D"] = D
@@ -653,6 +685,12 @@ def main():
     gram_flops = w.n * w.k * (w.k + 1)
     gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
     modes = gram_modes_measure(dp, Q, last["D"], args.pipeline_gram, stage["gram"], ws) if rank == 0 else None
+    lift = None
+    if rank == 0 and not args.no_extras:
+        try:
+            lift = lift_measure(dp, Q, offs, last["mean"], last["scale"], last["red"], res, w, mode)
+        except Exception as ex:  # reported, never fatal for the line
+            lift = {"error": str(ex)}
 
     # e2e: host snapshot matrices (pinned) -> device, the pipeline through the C ABI, results
     # back to pinned host memory every step.  Pipelined (the public StreamingPipeline): the
@@ -849,7 +887,8 @@ def main():
                 "timing": "CUDA events on the launching stream around the timed steps; inputs larger than L2",
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq,
-                "learn_double_word_rollouts": dw_roll, "paper_shape": paper, "batched_learn": batched}
+                "learn_double_word_rollouts": dw_roll, "step_v_lift": lift, "paper_shape": paper,
+                "batched_learn": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -321,6 +321,31 @@ int dopinf_rollout(const double* O, int r, int64_t ldo, const double* q0, int64_
                    int mode, double dt, double* Qtilde, int* finite, void* stream);
 
 /* ------------------------------------------------------------------------------------
+ * Step V (Section 3.6): the reduced solution in the original coordinates at chosen rows.
+ * V = Q[rows, :] T_r (rows of the POD basis, eq. MoS_POD_basis, from the transformed
+ * snapshots Q of Step II), then X[j, t] = scale(row_j) * (V[j, :] Qtilde[:, t]) + mean(row_j),
+ * the inverse of Step II's transform.  FP64 throughout.
+ *
+ * Q            n x k transformed snapshots (dtype, ld ldq >= n), as dopinf_transform left them.
+ * Tr           k x r (ld ldt >= k), from dopinf_reduce (its first r columns).
+ * Qtilde       r x n_t (ld ldqt >= r): column t = reduced state t, e.g. a dopinf_rollout
+ *              trajectory (n_t x r row-major is this layout with ldqt = r).
+ * rows         device, n_rows row indices in [0, n) (an index outside gives a NaN row of X), or
+ *              NULL for rows 0 .. n_rows - 1 (n_rows <= n).
+ * row_mean     optional (NULL: centring not undone), n doubles from dopinf_transform.
+ * var_scale    optional (NULL: scaling not undone), n_vars doubles from dopinf_transform, with
+ *              var_row_offsets (host, n_vars + 1, as for dopinf_transform; also used by row_mean
+ *              when given, else rows of one variable).
+ * X            out, n_rows x n_t column-major (ld ldx >= n_rows).
+ * Asynchronous.  Workspace: dopinf_lift_workspace(n_rows, r) bytes (the rows of V).
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_lift_workspace(int64_t n_rows, int r);
+int dopinf_lift(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, const double* Tr, int64_t ldt, int r,
+                const double* Qtilde, int64_t ldqt, int64_t n_t, const int64_t* rows, int64_t n_rows,
+                const double* row_mean, const double* var_scale, int n_vars, const int64_t* var_row_offsets,
+                double* X, int64_t ldx, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------
  * Learned proposal of (beta1, beta2, r).  The paper picks (beta1, beta2) by the grid search
  * of Section 3.5 and r by the retained energy of eq. ret_energy; this network proposes the
  * grid indices from statistics of the reduced data, and the grid search stays its fallback.

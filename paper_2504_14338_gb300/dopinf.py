@@ -78,6 +78,10 @@ def _load():
                                         _c_sz, _c_p]),
         "dopinf_learn_operator_offset": (_c_sz, [_c_i64, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int]),
+        "dopinf_lift_workspace": (_c_sz, [_c_i64, ctypes.c_int]),
+        "dopinf_lift": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, _c_p, _c_i64, ctypes.c_int, _c_p,
+                                       _c_i64, _c_i64, _c_p, _c_i64, _c_p, _c_p, ctypes.c_int, ctypes.POINTER(_c_i64),
+                                       _c_p, _c_i64, _c_p, _c_sz, _c_p]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_test_expire_waits": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows_large": (ctypes.c_int, [ctypes.c_int]),
@@ -366,6 +370,39 @@ def dopinf_rollout(O, q0, n_steps, mode=DISCRETE, dt=1.0, stream=None):
     _check("dopinf_rollout", lib.dopinf_rollout(_ptr(O), r, O.stride(1) if d > 1 else r, _ptr(q0), int(n_steps),
                                                 int(mode), float(dt), _ptr(Qt), _ptr(fin), _stream(stream)))
     return Qt, fin
+
+
+def dopinf_lift(Q, Tr, Qtilde, rows=None, n_rows=None, row_mean=None, var_scale=None, var_row_offsets=None,
+                ws=None, stream=None):
+    """Step V: the reduced solution lifted at chosen rows.  Q: (n, k) column-major transformed
+    snapshots; Tr: (k, r) column-major; Qtilde: (r, n_t) column-major (a (n_t, r) row-major
+    trajectory .t() is one); rows: int64 device tensor of row indices, or None for the first
+    n_rows rows (default all).  Returns X (n_rows, n_t) column-major."""
+    n, k, ldq = _colmajor(Q)
+    if Tr.stride(0) != 1 or Qtilde.stride(0) != 1:
+        raise ValueError("Tr and Qtilde must be column-major")
+    r = Tr.shape[1]
+    n_t = Qtilde.shape[1]
+    if Qtilde.shape[0] != r:
+        raise ValueError("Qtilde must have r rows")
+    if rows is not None:
+        rows = rows.to(device=Q.device, dtype=torch.int64).contiguous()
+        nr = rows.numel()
+    else:
+        nr = n if n_rows is None else int(n_rows)
+    X = torch.empty(n_t, nr, dtype=torch.float64, device=Q.device).t()
+    offs = None
+    n_vars = 0
+    if var_row_offsets is not None:
+        n_vars = len(var_row_offsets) - 1
+        offs = (_c_i64 * len(var_row_offsets))(*[int(v) for v in var_row_offsets])
+    nb = lib.dopinf_lift_workspace(nr, r)
+    buf, nb = _ws(nb, ws, Q.device)
+    _check("dopinf_lift", lib.dopinf_lift(_ptr(Q), _dtype_code(Q), n, k, ldq, _ptr(Tr), Tr.stride(1) if r > 1 else k,
+                                          r, _ptr(Qtilde), Qtilde.stride(1) if n_t > 1 else r, n_t, _ptr(rows), nr,
+                                          _ptr(row_mean), _ptr(var_scale), n_vars, offs, _ptr(X), X.stride(1)
+                                          if n_t > 1 else nr, _ptr(buf), nb, _stream(stream)))
+    return X
 
 
 # ------------------------------------------------------------------------------ proposal network

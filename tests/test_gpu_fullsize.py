@@ -127,3 +127,23 @@ def test_learn_selected_candidate_and_sample(run):
         assert ref["valid"][0] == (st[c] == 0), (c, st[c], ref["growth"][0])
         if st[c] == 0:
             assert abs(err[c] - ref["train_err"][0]) <= tol * ref["train_err"][0], (c, err[c], ref["train_err"][0])
+
+
+def test_lift_of_the_selected_rollout_at_sampled_rows(run):
+    """Step V at full size: the selected ROM's 5000-step rollout lifted at the 3006 sampled rows
+    (the paper lifts at probe rows) against the oracle's lift of the same inputs."""
+    from oracle import dopinf_oracle as Or
+    dp, w, res, red, Q, rows = run["dp"], run["w"], run["res"], run["red"], run["Q"], run["rows"]
+    r = res["r"]
+    traj, fin = dp.dopinf_rollout(res["O"], red["Qhat"][:r, 0].contiguous(), w.n_steps, mode=dp.CONTINUOUS_RK4,
+                                  dt=w.snap_dt)
+    assert int(fin.item()) == 1
+    Tr = red["Tr"][:, :r]
+    X = dp.dopinf_lift(Q, Tr, traj.t(), rows=torch.from_numpy(rows), row_mean=run["mean"], var_scale=run["scale"],
+                       var_row_offsets=w.var_row_offsets()).cpu().numpy()
+    Qs = Q[torch.from_numpy(rows).cuda()].cpu().numpy()
+    sc = run["scale"].cpu().numpy()[rows // w.n_per_var]
+    ref = Or.lift(Qs, Tr.cpu().numpy(), traj.cpu().numpy().T, np.arange(len(rows))) * sc[:, None] \
+        + run["mean"].cpu().numpy()[rows][:, None]
+    err = np.abs(X - ref).max(axis=1)
+    assert np.all(err <= 1e-11 * np.abs(ref).max(axis=1) + 1e-12 * sc), err.max()
