@@ -741,6 +741,23 @@ def main():
             outs = [o.cpu() for o in (res2["train_err"], res2["status"], res2["O_best"])]
         torch.cuda.synchronize()
         e2e["serial_value"] = world / ((time.perf_counter() - s0) / n_e2e)
+        # the out-of-core Gram: the raw matrix streamed from pinned host memory in 8 row blocks
+        # (the upload of block c + 1 under the Gram of block c), as for a matrix beyond HBM
+        if rank == 0 and not args.no_extras:
+            try:
+                chunk = (w.n + 7) // 8
+                dp.dopinf_gram_host(host_raw.t(), chunk, mode=pipe_mode, ws=ws)
+                ts = []
+                for _ in range(3):
+                    s1 = time.perf_counter()
+                    dp.dopinf_gram_host(host_raw.t(), chunk, mode=pipe_mode, ws=ws)
+                    ts.append(time.perf_counter() - s1)
+                gh = min(ts)
+                e2e["out_of_core_gram"] = {"ms": gh * 1e3, "blocks": 8, "mode": args.pipeline_gram,
+                                           "host_gbs": host_raw.numel() * host_raw.element_size() / gh / 1e9,
+                                           "device_gram_ms": stage["gram"]}
+            except Exception as ex:
+                e2e["out_of_core_gram"] = {"error": str(ex)}
 
     peaks = {}
     try:

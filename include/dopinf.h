@@ -56,6 +56,7 @@ enum dopinf_dtype { DOPINF_F64 = 0, DOPINF_F32 = 1 };
 
 #define DOPINF_CENTER 1u
 #define DOPINF_SCALE 2u
+#define DOPINF_SCALE_STD 4u  /* scale by the standard deviation of the centred variable instead */
 
 enum dopinf_gram_mode {
   DOPINF_GRAM_FP64 = 0,      /* FP64 FMA over every row (the plain path) */
@@ -106,7 +107,10 @@ int dopinf_test_expire_waits(int which);
  * Q            in/out, n x k, element type dtype, leading dimension ldq >= n (elements).
  * n_vars       number of variable blocks (1..64).
  * var_row_offsets host, n_vars + 1 nondecreasing row offsets, [0] = 0, [n_vars] = n.
- * flags        DOPINF_CENTER | DOPINF_SCALE.
+ * flags        DOPINF_CENTER | DOPINF_SCALE, or DOPINF_CENTER | DOPINF_SCALE_STD: the other
+ *              scaling Section 3.3 names, var_scale[j] = sqrt(sum c^2 / (rows_j k)) over the
+ *              variable's centred values c (FP64 sums: per row in time order, rows in a fixed
+ *              order; rounded to FP32 for FP32 data), then the same division as below.
  * row_mean     out, n doubles: mean_i = (sum_t Q[i,t], summed in t order in FP64) / k.
  * var_scale    out, n_vars doubles: max_{i in var, t} |Q[i,t] - mean_i|, rounded as the
  *              centred values are (FP64 data: FP64; FP32 data: fp32(fp64(x) - mean));
@@ -115,7 +119,8 @@ int dopinf_test_expire_waits(int which);
  *              FP32: Q = fp32(fp64(Q) - mean) / fp32(scale), the division in FP32.
  *              Bit-identical to the definition (no reassociation, no contraction).
  * dev_flags    optional device unsigned int; DOPINF_FLAG_* bits are OR-ed in.
- * Workspace:   dopinf_transform_workspace(n, n_vars) bytes.
+ * Workspace:   dopinf_transform_workspace(n, n_vars) bytes (may be NULL when dev_flags is given
+ *              and DOPINF_SCALE_STD is not).
  * ------------------------------------------------------------------------------------ */
 size_t dopinf_transform_workspace(int64_t n, int n_vars);
 int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int n_vars,
@@ -168,6 +173,24 @@ int dopinf_gram(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int
 int dopinf_gram_async(const void* Q, int dtype, int64_t n, int64_t k, int64_t ldq, int mode,
                       int accumulate, double* D, int64_t ldd, unsigned* dev_flags, void* ws,
                       size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Out-of-core Gram (Section 3.4, eq. mos_partitioned): D = Q^T Q (or D += Q^T Q) for a
+ * snapshot matrix Q that stays in HOST memory (n x k, dtype, column-major, ld ldq >= n),
+ * e.g. one larger than the device.  Row blocks of chunk_rows rows are copied into two device
+ * buffers of the workspace on a copy stream of the library's own and accumulated into D (in
+ * device memory) on `stream` with the Gram of `mode`, the upload of block c + 1 overlapping the
+ * Gram of block c.  Q_host should be page-locked (cudaHostAlloc / cudaHostRegister) for the
+ * copies to overlap.  Synchronises the stream; returns DOPINF_E_TIMEOUT / DOPINF_E_NONFINITE
+ * as dopinf_gram does.  The copy stream is one per device: calls on one device from several
+ * host threads at once are not supported.  Results: the partitioned sum in block order (the
+ * same value class as dopinf_gram; bits may differ from a single call, whose row partition
+ * differs).
+ * Workspace: dopinf_gram_host_workspace(chunk_rows, k, dtype, mode) bytes.
+ * ------------------------------------------------------------------------------------ */
+size_t dopinf_gram_host_workspace(int64_t chunk_rows, int64_t k, int dtype, int mode);
+int dopinf_gram_host(const void* Q_host, int dtype, int64_t n, int64_t k, int64_t ldq, int mode, int accumulate,
+                     double* D, int64_t ldd, int64_t chunk_rows, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------
  * Allocation-free FP64 Gram.  The paper has no counterpart: this entry point exists for

@@ -49,11 +49,13 @@ ZERO_SCALE = 2
 # --------------------------------------------------------------------------------------
 # Step II (Section 3.3): centering by the temporal mean, max-abs scaling per variable.
 # --------------------------------------------------------------------------------------
-def transform(Q, var_row_offsets, center=True, scale=True):
+def transform(Q, var_row_offsets, center=True, scale=True, scaling="maxabs"):
     """Centre each row by its temporal mean and scale each variable by its max-abs.
 
     Q: (n, k) float64 or float32 array, rows stacked variable-major.
     var_row_offsets: n_vars + 1 row offsets; variable j owns rows [off[j], off[j+1]).
+    scaling: "maxabs" (the Step II code) or "std", the other strategy Section 3.3 names: the
+    standard deviation of the variable's centred values, sqrt(sum c^2 / (rows * k)), in FP64.
     Returns (Q_transformed (same dtype), row_mean float64 (n,), var_scale float64 (n_vars,),
     flags) where flags has NONFINITE / ZERO_SCALE bits.
     """
@@ -81,7 +83,11 @@ def transform(Q, var_row_offsets, center=True, scale=True):
             block = Q[a:b, :]
             if block.size == 0:
                 continue
-            s = max(abs(block.min()), abs(block.max()))
+            if scaling == "std":
+                c = block.astype(np.float64)
+                s = Q.dtype.type(np.sqrt(np.sum(c * c) / c.size))
+            else:
+                s = max(abs(block.min()), abs(block.max()))
             if not np.isfinite(s):
                 flags |= NONFINITE
             if s == 0:

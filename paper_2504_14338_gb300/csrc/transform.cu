@@ -1,5 +1,6 @@
 // Step II of dOpInf (Section 3.3): per-row temporal centering and per-variable max-abs
-// scaling of the snapshot matrix, as two streaming passes over Q.
+// scaling of the snapshot matrix, as two streaming passes over Q (a third one for the
+// standard-deviation scaling, the other strategy the section names).
 //
 //  pass 1 (stats):  per row i, the FP64 sum over t in time order, the min and the max.
 //                   mean_i = sum / k.  Because rounding to nearest is monotone,
@@ -201,6 +202,59 @@ __global__ void __launch_bounds__(256) apply_kernel(T* __restrict__ Q, int64_t n
   }
 }
 
+// Standard-deviation scaling (DOPINF_SCALE_STD): per row the sum over t, in time order, of the
+// squared centred values (centred exactly as the apply pass centres them).
+template <typename T>
+__global__ void __launch_bounds__(256) rowsq_kernel(const T* __restrict__ Q, int64_t n, int64_t k, int64_t ldq,
+                                                    const double* __restrict__ mean, int center,
+                                                    double* __restrict__ rowsq) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double m = center ? mean[i] : 0.0;
+  double s = 0.0;
+  for (int64_t t = 0; t < k; ++t) {
+    const T x = Q[i + t * ldq];
+    double c;
+    if constexpr (sizeof(T) == 8)
+      c = center ? __dsub_rn(x, m) : x;
+    else
+      c = center ? (double)(float)((double)x - m) : (double)x;
+    s = __dadd_rn(s, __dmul_rn(c, c));
+  }
+  rowsq[i] = s;
+}
+
+// One CTA per variable: the rows' sums in a fixed order (each thread a strided sequence, then a
+// fixed tree), s_j = sqrt(total / (rows * k)), rounded to FP32 for FP32 data; a zero scale
+// becomes 1 (flagged), a non-finite one is flagged.
+__global__ void __launch_bounds__(256) var_std_kernel(const double* __restrict__ rowsq, VarTable vt, int64_t k,
+                                                      int f32, double* __restrict__ var_scale,
+                                                      unsigned* __restrict__ flags) {
+  __shared__ double sh[256];
+  const int v = blockIdx.x;
+  const int64_t a = vt.off[v], b = vt.off[v + 1];
+  double s = 0.0;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) s += rowsq[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double cnt = (double)(b - a) * (double)k;
+    double sd = cnt > 0.0 ? sqrt(sh[0] / cnt) : 0.0;
+    if (f32) sd = (double)(float)sd;
+    if (!isfinite(sd)) {
+      atomicOr(flags, DOPINF_FLAG_NONFINITE);
+    } else if (sd == 0.0) {
+      atomicOr(flags, DOPINF_FLAG_ZERO_SCALE);
+      sd = 1.0;
+    }
+    var_scale[v] = sd;
+  }
+}
+
 }  // namespace
 
 }  // namespace dopinf
@@ -208,10 +262,10 @@ __global__ void __launch_bounds__(256) apply_kernel(T* __restrict__ Q, int64_t n
 using namespace dopinf;
 
 DOPINF_API size_t dopinf_transform_workspace(int64_t n, int n_vars) {
-  (void)n;
   (void)n_vars;
   Carver c(nullptr);
   c.take<unsigned>(1);
+  c.take<double>(n > 0 ? (size_t)n : 1);  // per-row sums of squares (standard-deviation scaling)
   return c.used;
 }
 
@@ -222,7 +276,9 @@ DOPINF_API int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_
   if (dtype != DOPINF_F64 && dtype != DOPINF_F32) return DOPINF_E_ARG;
   if (n < 0 || k < 1 || ldq < (n > 1 ? n : 1) || n_vars < 1 || n_vars > kMaxVars) return DOPINF_E_ARG;
   if (!var_row_offsets || !row_mean || !var_scale || (n > 0 && !Q)) return DOPINF_E_ARG;
-  if (flags & ~(DOPINF_CENTER | DOPINF_SCALE)) return DOPINF_E_ARG;
+  if (flags & ~(DOPINF_CENTER | DOPINF_SCALE | DOPINF_SCALE_STD)) return DOPINF_E_ARG;
+  if ((flags & DOPINF_SCALE) && (flags & DOPINF_SCALE_STD)) return DOPINF_E_ARG;
+  const int std_scale = (flags & DOPINF_SCALE_STD) != 0;
   VarTable vt;
   vt.n_vars = n_vars;
   for (int v = 0; v <= n_vars; ++v) {
@@ -230,14 +286,16 @@ DOPINF_API int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_
     if (v > 0 && vt.off[v] < vt.off[v - 1]) return DOPINF_E_ARG;
   }
   if (vt.off[0] != 0 || vt.off[n_vars] != n) return DOPINF_E_ARG;
-  if (!dev_flags) {
+  if (!dev_flags || std_scale) {
     if (!ws || ws_bytes < dopinf_transform_workspace(n, n_vars) || misaligned(ws)) return DOPINF_E_ARG;
   }
   cudaStream_t st = as_stream(stream);
   Carver cv(ws);
+  unsigned* fl_ws = cv.take<unsigned>(1);
+  double* rowsq = cv.take<double>(n > 0 ? (size_t)n : 1);
   unsigned* fl = dev_flags;
   if (!fl) {
-    fl = cv.take<unsigned>(1);
+    fl = fl_ws;
     DOPINF_CUDA(cudaMemsetAsync(fl, 0, sizeof(unsigned), st));
   }
   int center = (flags & DOPINF_CENTER) != 0, scale = (flags & DOPINF_SCALE) != 0;
@@ -253,6 +311,19 @@ DOPINF_API int dopinf_transform(void* Q, int dtype, int64_t n, int64_t k, int64_
   }
   finalize_scale<<<(n_vars + 63) / 64, 64, 0, st>>>(var_scale, n_vars, scale, fl);
   DOPINF_TRY(launch_status());
+  if (std_scale) {
+    if (n > 0) {
+      const unsigned blocks = (unsigned)((n + 255) / 256);
+      if (dtype == DOPINF_F64)
+        rowsq_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(Q), n, k, ldq, row_mean, center, rowsq);
+      else
+        rowsq_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(Q), n, k, ldq, row_mean, center, rowsq);
+      DOPINF_TRY(launch_status());
+    }
+    var_std_kernel<<<n_vars, 256, 0, st>>>(rowsq, vt, k, dtype == DOPINF_F32, var_scale, fl);
+    DOPINF_TRY(launch_status());
+    scale = 1;
+  }
   if (n > 0 && (center || scale)) {
     int cols = 16;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)((k + cols - 1) / cols));

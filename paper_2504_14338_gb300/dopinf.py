@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libdopinf.so")
 OK, E_ARG, E_CUDA, E_NONFINITE, E_RANK, E_NO_STABLE, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -4, -6, -7, -8, -9
 FLAG_NONFINITE, FLAG_ZERO_SCALE, FLAG_TIMEOUT, FLAG_RANK, FLAG_NO_STABLE = 1, 2, 4, 8, 16
 F64, F32 = 0, 1
-CENTER, SCALE = 1, 2
+CENTER, SCALE, SCALE_STD = 1, 2, 4
 GRAM_FP64, GRAM_BF16X4, GRAM_OZAKI_FP64 = 0, 1, 2
 DISCRETE, CONTINUOUS_RK4 = 0, 1
 ROLLOUT_FP64, ROLLOUT_DW = 1, 2
@@ -82,6 +82,9 @@ def _load():
         "dopinf_lift": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, _c_p, _c_i64, ctypes.c_int, _c_p,
                                        _c_i64, _c_i64, _c_p, _c_i64, _c_p, _c_p, ctypes.c_int, ctypes.POINTER(_c_i64),
                                        _c_p, _c_i64, _c_p, _c_sz, _c_p]),
+        "dopinf_gram_host_workspace": (_c_sz, [_c_i64, _c_i64, ctypes.c_int, ctypes.c_int]),
+        "dopinf_gram_host": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int, _c_p,
+                                            _c_i64, _c_i64, _c_p, _c_sz, _c_p]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_test_expire_waits": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows_large": (ctypes.c_int, [ctypes.c_int]),
@@ -200,6 +203,24 @@ def dopinf_gram(Q, mode=GRAM_FP64, D=None, accumulate=False, ws=None, stream=Non
     # D is symmetric, so its row-major storage is its column-major storage
     _check("dopinf_gram", lib.dopinf_gram(_ptr(Q), _dtype_code(Q), n, k, ldq, mode, int(accumulate), _ptr(D),
                                           D.stride(0), _ptr(buf), nb, _stream(stream)))
+    return D
+
+
+def dopinf_gram_host(Q_host, chunk_rows, mode=GRAM_FP64, D=None, accumulate=False, ws=None, stream=None,
+                     device="cuda"):
+    """Out-of-core Gram of a snapshot matrix in host memory: Q_host is a CPU (n, k) column-major
+    tensor (pinned for overlapped copies), streamed in row blocks of chunk_rows; D (k x k FP64)
+    on the device."""
+    if Q_host.is_cuda:
+        raise ValueError("Q_host must be in host memory")
+    n, k, ldq = _colmajor(Q_host)
+    if D is None:
+        D = torch.zeros(k, k, dtype=torch.float64, device=device)
+    nb = lib.dopinf_gram_host_workspace(min(int(chunk_rows), n), k, _dtype_code(Q_host), mode)
+    buf, nb = _ws(nb, ws, D.device)
+    _check("dopinf_gram_host", lib.dopinf_gram_host(_ptr(Q_host), _dtype_code(Q_host), n, k, ldq, mode,
+                                                    int(accumulate), _ptr(D), D.stride(0), int(chunk_rows), _ptr(buf),
+                                                    nb, _stream(stream)))
     return D
 
 

@@ -75,6 +75,33 @@ def test_transform_bit_exact_f32(dp):
     assert np.array_equal(Q.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_transform_std_scaling_vs_oracle(dp, dtype):
+    """Standard-deviation scaling: the centring is bit-exact as before; the scale is an FP64
+    sum in another order than the oracle's (1e-13 relative; FP32 data then round it to FP32,
+    which may move it by one FP32 ulp); and given the GPU's scale the scaled values are the
+    oracle's steps bit for bit."""
+    rng = np.random.default_rng(31)
+    Qn = rng.standard_normal((3000, 41)) * np.repeat([1e-3, 1.0, 5e3], 1000)[:, None] + 2.0
+    if dtype == "f32":
+        Qn = Qn.astype(np.float32)
+    offs = [0, 1000, 2000, 3000]
+    Q = to_dev(dp, Qn)
+    mean, scale, flags = dp.dopinf_transform(Q, offs, flags=dp.CENTER | dp.SCALE_STD)
+    _, rmean, rscale, rflags = O.transform(Qn, offs, scaling="std")
+    assert np.array_equal(mean.cpu().numpy(), rmean)
+    sc = scale.cpu().numpy()
+    assert np.allclose(sc, rscale, rtol=1e-13 if dtype == "f64" else 1.2e-7, atol=0)
+    assert int(flags.item()) == rflags == 0
+    centred, _, _, _ = O.transform(Qn, offs, scale=False)
+    var = np.repeat(np.arange(3), 1000)
+    if dtype == "f64":
+        expect = centred / sc[var][:, None]
+    else:
+        expect = centred / sc[var][:, None].astype(np.float32)
+    assert np.array_equal(Q.cpu().numpy(), expect)
+
+
 def test_transform_bit_exact_at_the_ends_of_the_exponent_range(dp):
     """Centred values around 2^+-900 (where the division switches between Markstein's correction
     and the IEEE division), subnormals and mixed magnitudes: still the oracle's bits."""

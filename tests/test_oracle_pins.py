@@ -382,3 +382,22 @@ def test_lift_inverse_transform_by_hand():
     Qtilde = np.array([[1.0, 2.0], [3.0, 4.0]])
     X = O.lift(Q, Tr, Qtilde, [0, 1, 2], np.array([10.0, 20.0, 30.0]), np.array([2.0, 5.0]), [0, 2, 3])
     assert X.tolist() == [[12.0, 14.0], [26.0, 28.0], [30.0, 30.0]]
+
+
+def test_transform_std_scaling_closed_form():
+    """Scaling by the standard deviation of the centred variable (Section 3.3's alternative):
+    a variable whose centred values are +-a has standard deviation a; a constant variable is
+    left unscaled and flagged; afterwards every variable has unit RMS."""
+    Q = np.array([[1.0, 5.0, 1.0, 5.0], [10.0, 14.0, 10.0, 14.0], [7.0, 7.0, 7.0, 7.0]])
+    Qt, mean, scale, flags = O.transform(Q, [0, 2, 3], scaling="std")
+    assert scale.tolist() == [2.0, 1.0]
+    assert np.array_equal(Qt[:2], np.array([[-1.0, 1.0, -1.0, 1.0]] * 2))
+    assert flags == 2
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((500, 40)) * np.repeat([3e-3, 7e2], 250)[:, None] + 1.0
+    Rt, _, s, _ = O.transform(R, [0, 250, 500], scaling="std")
+    for a, b in [(0, 250), (250, 500)]:
+        assert abs(np.sqrt(np.mean(Rt[a:b] ** 2)) - 1.0) < 1e-13
+    # equals numpy's population standard deviation of the centred block
+    C = R - R.mean(axis=1, keepdims=True)
+    assert np.allclose(s, [C[:250].std(), C[250:].std()], rtol=1e-13)
