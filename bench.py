@@ -700,15 +700,18 @@ def main():
     if host_raw is not None:
         from paper_2504_14338_gb300.graph import StreamingPipeline
         # the upload alone (CUDA events), for reading the end-to-end number against
-        up = []
+        from paper_2504_14338_gb300.graph import upload
+        up, up1 = [], []
         for _ in range(3):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            QT.copy_(host_raw, non_blocking=True)
-            b.record(stream)
-            torch.cuda.synchronize()
-            up.append(a.elapsed_time(b))
+            for chunks, lst in ((8, up), (1, up1)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                upload(QT, host_raw, chunks)
+                b.record(stream)
+                torch.cuda.synchronize()
+                lst.append(a.elapsed_time(b))
         h2d_gbs = host_raw.numel() * host_raw.element_size() / (min(up) / 1e3) / 1e9
+        h2d_gbs_one = host_raw.numel() * host_raw.element_size() / (min(up1) / 1e3) / 1e9
         sp = StreamingPipeline(host_raw, offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt,
                                gram_mode=pipe_mode, device=dev)
         sp.run([host_raw] * max(2, args.warmup))
@@ -729,14 +732,14 @@ def main():
                       "(pinned host -> device, copy stream) overlapping step i's captured pipeline; every "
                       "step's results copied back to pinned host memory and read",
                "best_index": outs[-1]["best"], "flags": outs[-1]["flags"],
-               "h2d_gbs_alone": h2d_gbs, "host_cpus": host_cpus}
+               "h2d_gbs_alone": h2d_gbs, "h2d_gbs_alone_one_copy": h2d_gbs_one, "host_cpus": host_cpus}
         del sp, outs
         torch.cuda.empty_cache()
         # serial: copy, eager pipeline, read-back, one after the other
         torch.cuda.synchronize()
         s0 = time.perf_counter()
         for _ in range(n_e2e):
-            QT.copy_(host_raw, non_blocking=True)
+            upload(QT, host_raw)
             res2 = step()
             outs = [o.cpu() for o in (res2["train_err"], res2["status"], res2["O_best"])]
         torch.cuda.synchronize()

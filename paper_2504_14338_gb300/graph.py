@@ -170,6 +170,17 @@ def bind_host_to_device(device):
         return None
 
 
+def upload(dst, src, chunks=8):
+    """Host-to-device copy of a (k, n) snapshot block as `chunks` copies of consecutive
+    snapshots on the current stream (one copy engine request per chunk instead of one for the
+    whole matrix)."""
+    rows = dst.shape[0]
+    for c in range(chunks):
+        a, b = rows * c // chunks, rows * (c + 1) // chunks
+        if b > a:
+            dst[a:b].copy_(src[a:b], non_blocking=True)
+
+
 class StreamingPipeline:
     """Steps II-IV over snapshot matrices that arrive one after another in pinned host memory.
 
@@ -187,12 +198,13 @@ class StreamingPipeline:
 
     def __init__(self, host_QT, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE,
                  dt=1.0, gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2,
-                 device="cuda"):
+                 device="cuda", upload_chunks=8):
         """host_QT: pinned CPU tensor (k, n), row-major, i.e. the column-major n x k snapshot matrix;
         every submitted matrix has this shape and dtype.  The first one also serves for capture."""
         if not host_QT.is_pinned():
             raise ValueError("host_QT must be in pinned host memory")
         dev = torch.device(device)
+        self.upload_chunks = int(upload_chunks)
         self.QT = [torch.empty(host_QT.shape, dtype=host_QT.dtype, device=dev) for _ in range(2)]
         kw = dict(mode=mode, dt=dt, gram_mode=gram_mode, r_fixed=r_fixed, energy_target=energy_target,
                   max_growth=max_growth)
@@ -228,7 +240,7 @@ class StreamingPipeline:
         # the upload into copy b waits for the front graph that last read it (step i - 2)
         self.copy_stream.wait_event(self.front_done[b])
         with torch.cuda.stream(self.copy_stream):
-            self.QT[b].copy_(host_QT, non_blocking=True)
+            upload(self.QT[b], host_QT, self.upload_chunks)
             self.uploaded[b].record(self.copy_stream)
         self.stream.wait_event(self.uploaded[b])
         with torch.cuda.stream(self.stream):
