@@ -585,7 +585,8 @@ def main():
         if args.rows_large:
             dp.dopinf_tune_rollout_rows_large(args.rows_large)
         dp.dopinf_transform(Q, offs, ws=ws)
-        red = dp.dopinf_reduce(dp.dopinf_gram(Q, ws=ws), r_cap=r_max, r_fixed=r_max, ws=ws)
+        r_cap = max(r_list)
+        red = dp.dopinf_reduce(dp.dopinf_gram(Q, ws=ws), r_cap=r_cap, r_fixed=r_cap, ws=ws)
         times = []
         for i in range(args.warmup + args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
