@@ -30,9 +30,9 @@ METRIC = "Gram TFLOP/s + dOpInf learn time, split-prec/batched vs FP64 plain, at
 UNIT = "dOpInf pipelines/s"
 WORKLOAD = "stepflow"
 FP64_NOMINAL_TF, BF16_NOMINAL_TF = 1.25, 2250.0
-# DRAM bytes (read + write) per launch of the r = 30 rollout launch, from the ncu captures
-# summarised in profiles/ (None: not captured for the current kernel)
-ROLLOUT_TRAFFIC = {"dw": 8.3e6, "fp64": None}
+# DRAM bytes (read + write) of the rollout stage's three launches (r = 30, 20, 10), from the ncu
+# capture summarised in profiles/ (None: not captured for that arithmetic's kernels)
+ROLLOUT_TRAFFIC = {"dw": None, "fp64": 12.03e6}
 
 
 def parse():
@@ -805,8 +805,8 @@ def main():
         # DRAM bytes of one ncu capture of the r = 30 launch on the same r, k, grid and horizon
         # (the rollout's work does not depend on n): the operators, read once
         "traffic": ROLLOUT_TRAFFIC.get("fp64" if arith == dp.ROLLOUT_FP64 else "dw"),
-        "traffic_scope": "the r = 30 launch alone (the stage's largest; its operators, 7.6 MB, read once)",
-        "traffic_source": "profiles/rollout_cols_kernel_stepflow_learn.md",
+        "traffic_scope": "the three launches of the stage (r = 30, 20, 10): their operators, 10.3 MB, read once",
+        "traffic_source": "profiles/rollout_cols_kernel_fp64_stepflow.md",
         "algorithmic_flops_per_launch": roll_flops, "launch_ms": roll_ms,
         "rhs_evaluations": int(steps_run.sum()) * evals,
         "critical_path": "a valid candidate's %d steps x %d dependent evaluations, each closed by a cluster "
