@@ -885,6 +885,16 @@ def main():
             paper = paper_shape_measure(dp, synth, dev)
         except Exception as ex:
             paper = {"error": str(ex)}
+    proposal = None
+    if rank == 0 and not args.no_extras:
+        # the learned (beta1, beta2, r) proposal at a stated scale: trained on 240 seeded systems,
+        # judged on 60 held-out ones by the validation error of a held-out continuation window
+        try:
+            from paper_2504_14338_gb300 import proposal as P
+            spec = P.ProposalSpec(r_list=(5, 10, 15, 20, 30), r_true_range=(5, 30), k_range=(300, 800))
+            proposal = P.experiment(spec, 240, 60, steps=1500)
+        except Exception as ex:
+            proposal = {"error": str(ex)}
     batched = None
     if rank == 0 and not args.no_extras:
         try:
@@ -909,7 +919,7 @@ def main():
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq,
                 "learn_double_word_rollouts": dw_roll, "step_v_lift": lift, "paper_shape": paper,
-                "batched_learn": batched}
+                "batched_learn": batched, "proposal": proposal}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -400,6 +400,22 @@ int dopinf_mlp_train_step(float* params, float* adam_m, float* adam_v, int step,
                           const float* X, const int* labels, int batch, float* loss, float* grad_out, void* ws,
                           size_t ws_bytes, void* stream);
 
+/* Input standardisation of the network (the training set's statistics) and the ranking of the
+ * grid candidates by the network's output.
+ * dopinf_mlp_feature_stats: mu, sd (device, 64 doubles each) = per-feature mean and sample
+ *   standard deviation (ddof = 1, floored at 1e-6) of X (device, batch x 64 FP32, row-major).
+ * dopinf_mlp_standardize: Xs = fp32((X - mu) / sd) per feature (the arithmetic in FP64).
+ * dopinf_mlp_rank: for each row of logits (device, batch x (h1 + h2 + h3), the three heads of
+ *   dopinf_mlp_forward), the `top` candidates (i1, i2, i3) with the highest joint
+ *   log-probability log softmax_1(i1) + log softmax_2(i2) + log softmax_3(i3) (FP64), the lowest
+ *   flat index (i1 h2 + i2) h3 + i3 first on ties: ranked (device, batch x top x 3 ints; -1 past
+ *   the h1 h2 h3 candidates), score (optional, device, batch x top doubles).  h1 h2 h3 <= 4096,
+ *   top <= 64 (DOPINF_E_UNSUPPORTED above).  head_sizes: host, 3 ints.  All asynchronous. */
+int dopinf_mlp_feature_stats(const float* X, int batch, double* mu, double* sd, void* stream);
+int dopinf_mlp_standardize(const float* X, int batch, const double* mu, const double* sd, float* Xs, void* stream);
+int dopinf_mlp_rank(const float* logits, int batch, const int* head_sizes, int top, int* ranked, double* score,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

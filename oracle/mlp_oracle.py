@@ -149,3 +149,43 @@ def features(eigvals, trace, Qhat, k):
             f[52 + j] = np.mean(q ** 4) / (m2 * m2) - 1.5
     f[63] = math.log10(k)
     return f
+
+
+# --------------------------------------------------------------------------------------
+# Input standardisation and the ranking of grid candidates by the network's joint probability.
+# --------------------------------------------------------------------------------------
+def feature_stats(X, sd_floor=1e-6):
+    """Per-feature mean and sample standard deviation (ddof = 1, floored) of a training set."""
+    X = np.asarray(X, dtype=np.float64)
+    mu = X.mean(axis=0)
+    sd = np.maximum(X.std(axis=0, ddof=1), sd_floor) if X.shape[0] > 1 else np.full(X.shape[1], sd_floor)
+    return mu, sd
+
+
+def standardise(X, mu, sd):
+    """(x - mu) / sd per feature, in FP64, rounded to FP32 (the network's input type)."""
+    return ((np.asarray(X, dtype=np.float64) - mu) / sd).astype(np.float32)
+
+
+def log_softmax(z):
+    z = np.asarray(z, dtype=np.float64)
+    m = z.max(axis=-1, keepdims=True)
+    return z - (m + np.log(np.exp(z - m).sum(axis=-1, keepdims=True)))
+
+
+def rank_candidates(logits, heads, top):
+    """The `top` grid candidates (i1, i2, i3) of each row in decreasing joint log-probability
+    log p1(i1) + log p2(i2) + log p3(i3) (the three heads' softmaxes), ties to the lowest flat
+    index (i1 h2 + i2) h3 + i3.  Returns (indices (B, top, 3), scores (B, top))."""
+    L = np.asarray(logits, dtype=np.float64)
+    h1, h2, h3 = heads
+    lp1, lp2, lp3 = log_softmax(L[:, :h1]), log_softmax(L[:, h1:h1 + h2]), log_softmax(L[:, h1 + h2:h1 + h2 + h3])
+    idx = np.zeros((L.shape[0], top, 3), dtype=np.int64)
+    sc = np.zeros((L.shape[0], top))
+    for b in range(L.shape[0]):
+        joint = (lp1[b][:, None, None] + lp2[b][None, :, None] + lp3[b][None, None, :]).reshape(-1)
+        order = sorted(range(joint.size), key=lambda c: (-joint[c], c))[:top]
+        for t, c in enumerate(order):
+            idx[b, t] = (c // (h2 * h3), (c // h3) % h2, c % h3)
+            sc[b, t] = joint[c]
+    return idx, sc

@@ -271,10 +271,142 @@ int mlp_forward_impl(const float* params, int n_out, const float* X, int B, cons
   return DOPINF_OK;
 }
 
+// Per-feature mean and sample standard deviation (ddof = 1, floored at 1e-6) of a training
+// set X (batch x 64, row-major), FP64: one CTA per feature, each thread a strided sequence of
+// rows, then a fixed tree.
+__global__ void __launch_bounds__(256) feature_stats_kernel(const float* __restrict__ X, int batch,
+                                                            double* __restrict__ mu, double* __restrict__ sd) {
+  __shared__ double sh[256];
+  const int f = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < batch; b += blockDim.x) s += (double)X[(size_t)b * 64 + f];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double m = sh[0] / (double)batch;
+  __syncthreads();
+  double q = 0.0;
+  for (int b = threadIdx.x; b < batch; b += blockDim.x) {
+    const double c = (double)X[(size_t)b * 64 + f] - m;
+    q += c * c;
+  }
+  sh[threadIdx.x] = q;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    mu[f] = m;
+    const double v = batch > 1 ? sqrt(sh[0] / (double)(batch - 1)) : 0.0;
+    sd[f] = v > 1e-6 ? v : 1e-6;
+  }
+}
+
+// Xs = fp32((x - mu) / sd), the subtraction and division in FP64.
+__global__ void standardise_kernel(const float* __restrict__ X, int n, const double* __restrict__ mu,
+                                   const double* __restrict__ sd, float* __restrict__ Xs) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int f = e % 64;
+  Xs[e] = (float)(((double)X[e] - mu[f]) / sd[f]);
+}
+
+constexpr int kRankMax = 4096;  // candidates of the joint ranking (h1 h2 h3)
+
+// One CTA per row of logits: per-head log-softmax in FP64, the joint log-probability of every
+// (i1, i2, i3), and `top` rounds of a block argmax (highest score, lowest flat index on ties).
+__global__ void __launch_bounds__(256) rank_kernel(const float* __restrict__ logits, int n_out, int h1, int h2, int h3,
+                                                   int top, int* __restrict__ ranked, double* __restrict__ score) {
+  __shared__ double lse[3];
+  __shared__ double joint[kRankMax];
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  const float* z = logits + (size_t)blockIdx.x * n_out;
+  const int hs[3] = {h1, h2, h3}, ho[3] = {0, h1, h1 + h2};
+  if (threadIdx.x < 3) {
+    const int h = threadIdx.x;
+    double m = -INFINITY;
+    for (int i = 0; i < hs[h]; ++i) m = fmax(m, (double)z[ho[h] + i]);
+    double s = 0.0;
+    for (int i = 0; i < hs[h]; ++i) s += exp((double)z[ho[h] + i] - m);
+    lse[h] = m + log(s);
+  }
+  __syncthreads();
+  const int n = h1 * h2 * h3;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const int i1 = c / (h2 * h3), i2 = (c / h3) % h2, i3 = c % h3;
+    joint[c] = ((double)z[i1] - lse[0]) + ((double)z[h1 + i2] - lse[1]) + ((double)z[h1 + h2 + i3] - lse[2]);
+  }
+  __syncthreads();
+  for (int t = 0; t < top; ++t) {
+    double v = -INFINITY;
+    int idx = 0x7fffffff;
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+      if (joint[c] > v || (joint[c] == v && c < idx)) {
+        v = joint[c];
+        idx = c;
+      }
+    bv[threadIdx.x] = v;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) {
+        const double v2 = bv[threadIdx.x + h];
+        const int i2 = bi[threadIdx.x + h];
+        if (v2 > bv[threadIdx.x] || (v2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+          bv[threadIdx.x] = v2;
+          bi[threadIdx.x] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const int c = bi[0];
+      int* o = ranked + ((size_t)blockIdx.x * top + t) * 3;
+      const bool ok = c < n;
+      o[0] = ok ? c / (h2 * h3) : -1;
+      o[1] = ok ? (c / h3) % h2 : -1;
+      o[2] = ok ? c % h3 : -1;
+      if (score) score[(size_t)blockIdx.x * top + t] = ok ? bv[0] : -INFINITY;
+      if (ok) joint[c] = NAN;  // excluded from the next rounds: NaN wins no comparison
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 }  // namespace dopinf
 
 using namespace dopinf;
+
+DOPINF_API int dopinf_mlp_feature_stats(const float* X, int batch, double* mu, double* sd, void* stream) {
+  if (!X || batch < 1 || !mu || !sd) return DOPINF_E_ARG;
+  feature_stats_kernel<<<64, 256, 0, as_stream(stream)>>>(X, batch, mu, sd);
+  return launch_status();
+}
+
+DOPINF_API int dopinf_mlp_standardize(const float* X, int batch, const double* mu, const double* sd, float* Xs,
+                                      void* stream) {
+  if (!X || batch < 1 || !mu || !sd || !Xs || batch > (1 << 24)) return DOPINF_E_ARG;
+  const int n = batch * 64;
+  standardise_kernel<<<(n + 255) / 256, 256, 0, as_stream(stream)>>>(X, n, mu, sd, Xs);
+  return launch_status();
+}
+
+DOPINF_API int dopinf_mlp_rank(const float* logits, int batch, const int* head_sizes, int top, int* ranked,
+                               double* score, void* stream) {
+  if (!logits || batch < 1 || !head_sizes || top < 1 || !ranked) return DOPINF_E_ARG;
+  for (int h = 0; h < 3; ++h)
+    if (head_sizes[h] < 1) return DOPINF_E_ARG;
+  const int h1 = head_sizes[0], h2 = head_sizes[1], h3 = head_sizes[2];
+  if ((int64_t)h1 * h2 * h3 > kRankMax || top > 64 || batch > 65535) return DOPINF_E_UNSUPPORTED;
+  rank_kernel<<<batch, 256, 0, as_stream(stream)>>>(logits, h1 + h2 + h3, h1, h2, h3, top, ranked, score);
+  return launch_status();
+}
 
 DOPINF_API size_t dopinf_mlp_param_count(int n_out) { return n_out > 0 ? mlp_layout(n_out).count : 0; }
 

@@ -85,6 +85,10 @@ def _load():
         "dopinf_gram_host_workspace": (_c_sz, [_c_i64, _c_i64, ctypes.c_int, ctypes.c_int]),
         "dopinf_gram_host": (ctypes.c_int, [_c_p, ctypes.c_int, _c_i64, _c_i64, _c_i64, ctypes.c_int, ctypes.c_int, _c_p,
                                             _c_i64, _c_i64, _c_p, _c_sz, _c_p]),
+        "dopinf_mlp_feature_stats": (ctypes.c_int, [_c_p, ctypes.c_int, _c_p, _c_p, _c_p]),
+        "dopinf_mlp_standardize": (ctypes.c_int, [_c_p, ctypes.c_int, _c_p, _c_p, _c_p, _c_p]),
+        "dopinf_mlp_rank": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _c_p, _c_p,
+                                           _c_p]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_test_expire_waits": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows_large": (ctypes.c_int, [ctypes.c_int]),
@@ -464,3 +468,36 @@ def dopinf_mlp_train_step(params, m, v, step, lr, head_sizes, X, labels, want_gr
                                                               _ptr(X.contiguous()), _ptr(labels.contiguous()), B,
                                                               _ptr(loss), _ptr(grad), _ptr(buf), nb, _stream(stream)))
     return loss, grad
+
+
+def dopinf_mlp_feature_stats(X, stream=None):
+    """Per-feature mean and sample standard deviation (floored at 1e-6) of X (batch x 64 FP32):
+    two FP64 device tensors of 64."""
+    X = X.contiguous()
+    mu = torch.empty(64, dtype=torch.float64, device=X.device)
+    sd = torch.empty(64, dtype=torch.float64, device=X.device)
+    _check("dopinf_mlp_feature_stats", lib.dopinf_mlp_feature_stats(_ptr(X), X.shape[0], _ptr(mu), _ptr(sd),
+                                                                    _stream(stream)))
+    return mu, sd
+
+
+def dopinf_mlp_standardize(X, mu, sd, stream=None):
+    """(X - mu) / sd per feature (FP64 arithmetic, FP32 result)."""
+    X = X.contiguous()
+    Xs = torch.empty_like(X)
+    _check("dopinf_mlp_standardize", lib.dopinf_mlp_standardize(_ptr(X), X.shape[0], _ptr(mu.contiguous()),
+                                                                _ptr(sd.contiguous()), _ptr(Xs), _stream(stream)))
+    return Xs
+
+
+def dopinf_mlp_rank(logits, head_sizes, top, stream=None):
+    """The `top` grid candidates of each row by joint log-probability: (ranked (batch, top, 3)
+    int32, score (batch, top) float64), device tensors."""
+    logits = logits.contiguous()
+    B = logits.shape[0]
+    hs = (ctypes.c_int * 3)(*[int(h) for h in head_sizes])
+    ranked = torch.empty(B, top, 3, dtype=torch.int32, device=logits.device)
+    score = torch.empty(B, top, dtype=torch.float64, device=logits.device)
+    _check("dopinf_mlp_rank", lib.dopinf_mlp_rank(_ptr(logits), B, hs, int(top), _ptr(ranked), _ptr(score),
+                                                  _stream(stream)))
+    return ranked, score

@@ -1,13 +1,30 @@
 """Learned proposal of (beta1, beta2, r), trained on grid-search outcomes of seeded systems.
 
 Each seeded system (a synthetic quadratic system of dimension r_true lifted to n rows) goes
-through Steps II-III on the GPU; its 64 features come from the eigenvalues and the reduced
-data, its label is the (beta1 index, beta2 index, r index) the full grid search of Step IV
-selects.  The network is trained with the library's own forward/backward/Adam kernels.  At
-use, the proposal is verified by a single-candidate learn step (one Cholesky solve and one
-rollout); if that candidate is not valid the next most probable candidates are tried and, as
-the last resort, the full grid search runs.  Every step runs in the CUDA library.
+through Steps II-III on the GPU on its training window of k snapshots; its 64 features come from
+the eigenvalues and the reduced data, its label is the (beta1 index, beta2 index, r index) the
+full grid search of Step IV selects.  The network is trained with the library's own
+forward/backward/Adam kernels on inputs standardised by the library (the training set's
+statistics).  At use, the library ranks the grid candidates by the network's joint probability;
+the most probable is verified by a single-candidate learn step (one Cholesky solve and one
+rollout); if that candidate is not valid the next ones are tried and, as the last resort, the
+full grid search runs.
+
+The judge of a selection is its validation error: the selected ROM is rolled out past the
+training window over a held-out continuation of the true trajectory (val_frac * k further
+snapshots), lifted to the transformed snapshot coordinates with Step V, and compared with the
+held-out snapshots transformed with the training window's mean and scale: the largest relative
+2-norm error over the held-out instants.  Every step of the method runs in the CUDA library; the
+validation error's final norms are evaluation arithmetic on the lifted states.
+
+Systems are generated by worker processes (spawned: they touch no GPU), so large training sets
+do not wait on the host.  `python -m paper_2504_14338_gb300.proposal --train N --eval M` runs the
+whole experiment and prints one JSON line.
 """
+import argparse
+import json
+import multiprocessing as mp
+import os
 import time
 from dataclasses import dataclass
 
@@ -28,7 +45,8 @@ class ProposalSpec:
     r_true_range: tuple = (5, 30)
     k_range: tuple = (200, 400)
     n_per_var: int = 1000
-    steps_factor: int = 2      # rollout length = steps_factor * k
+    steps_factor: int = 2      # grid-search rollout length = steps_factor * k
+    val_frac: float = 0.25     # held-out continuation: val_frac * k snapshots after the training window
     r_cap: int = 40            # eigenpairs computed (features use lambda_2..lambda_33)
     mode: int = dp.DISCRETE
 
@@ -44,22 +62,46 @@ class ProposalSpec:
 
 
 def system(spec, seed):
+    """(workload with k_train + k_val snapshots, k_train) of one seeded system."""
     rng = np.random.default_rng(seed)
     r_true = int(rng.integers(spec.r_true_range[0], spec.r_true_range[1] + 1))
     k = int(rng.integers(spec.k_range[0], spec.k_range[1] + 1))
-    return synth.Workload("proposal", 2, spec.n_per_var, k, r_true, seed=seed)
+    k_val = max(1, int(round(spec.val_frac * k)))
+    return synth.Workload("proposal", 2, spec.n_per_var, k + k_val, r_true, seed=seed), k
 
 
-def reduced(spec, w, ws, device="cuda"):
-    """Steps II-III of one system on the GPU: (eigvals, trace, Qhat)."""
+def _generate(args):
+    spec, seed = args
+    w, k = system(spec, seed)
     Qn, _ = synth.snapshots_numpy(w)
-    Q = dp.snapshot_matrix(w.n, w.k, device=device)
-    Q.copy_(torch.from_numpy(np.asarray(Qn)))
-    dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
+    return seed, w, k, np.asarray(Qn)
+
+
+def generated(spec, seeds, workers=None):
+    """Yields (seed, workload, k_train, snapshots (n, k_train + k_val)) in seed order, made by a pool
+    of spawned worker processes (started before any of them is consumed)."""
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    seeds = list(seeds)
+    if workers == 1 or len(seeds) < 4:
+        for s in seeds:
+            yield _generate((spec, s))
+        return
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for item in pool.imap(_generate, [(spec, s) for s in seeds], chunksize=2):
+            yield item
+
+
+def reduced(spec, w, k, Qn, ws, device="cuda"):
+    """Steps II-III of one system's training window on the GPU.  Returns a dict: eigvals, trace,
+    Qhat, Tr, the transformed training snapshots Q and the transform's mean and scale."""
+    Q = dp.snapshot_matrix(w.n, k, device=device)
+    Q.copy_(torch.from_numpy(np.ascontiguousarray(Qn[:, :k])))
+    mean, scale, _ = dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
     D = dp.dopinf_gram(Q, ws=ws)
-    r_cap = min(spec.r_cap, w.k - 1)
+    r_cap = min(spec.r_cap, k - 1)
     red = dp.dopinf_reduce(D, r_cap=r_cap, r_fixed=r_cap, ws=ws)
-    return red["eigvals"], red["trace"], red["Qhat"]
+    return dict(eigvals=red["eigvals"], trace=red["trace"], Qhat=red["Qhat"], Tr=red["Tr"], Q=Q, mean=mean,
+                scale=scale)
 
 
 def grid_search(spec, Qhat, k, ws):
@@ -67,19 +109,18 @@ def grid_search(spec, Qhat, k, ws):
                            mode=spec.mode, dt=1.0, ws=ws)
 
 
-def dataset(spec, seeds, ws):
+def dataset(spec, seeds, ws, workers=None):
     """Features (N x 64, device) and labels (N x 3, device) of the systems with a valid grid optimum."""
     feats, labels, kept = [], [], []
     nb = spec.n_b1 * spec.n_b2
-    for s in seeds:
-        w = system(spec, s)
-        lam, tr, Qh = reduced(spec, w, ws)
-        res = grid_search(spec, Qh, w.k, ws)
+    for s, w, k, Qn in generated(spec, seeds, workers):
+        red = reduced(spec, w, k, Qn, ws)
+        res = grid_search(spec, red["Qhat"], k, ws)
         if res["best"] < 0:
             continue
         b = res["best"]
         labels.append([(b % nb) // spec.n_b2, b % spec.n_b2, b // nb])
-        feats.append(dp.dopinf_proposal_features(lam, tr, Qh))
+        feats.append(dp.dopinf_proposal_features(red["eigvals"], red["trace"], red["Qhat"]))
         kept.append(s)
     X = torch.stack(feats)
     y = torch.tensor(labels, dtype=torch.int32, device=X.device)
@@ -97,18 +138,11 @@ def init_params(n_out, seed=0, device="cuda"):
     return torch.from_numpy(np.concatenate(parts).astype(np.float32)).to(device)
 
 
-def _standardise(X, mu, sd):
-    """Host-side input scaling of the (small) feature matrix."""
-    Xh = X.cpu().numpy().astype(np.float64)
-    return torch.from_numpy(((Xh - mu) / sd).astype(np.float32)).to(X.device).contiguous()
-
-
 def train(spec, X, y, steps=1500, batch=64, lr=1e-3, seed=0):
-    """Adam on the GPU (library kernels); inputs standardised with the training statistics."""
-    Xh = X.cpu().numpy().astype(np.float64)
-    mu = Xh.mean(axis=0)
-    sd = np.maximum(Xh.std(axis=0, ddof=1), 1e-6)
-    Xs = _standardise(X, mu, sd)
+    """Adam on the GPU (library kernels); inputs standardised by the library with the training
+    set's statistics."""
+    mu, sd = dp.dopinf_mlp_feature_stats(X)
+    Xs = dp.dopinf_mlp_standardize(X, mu, sd)
     n_out = sum(spec.heads)
     params = init_params(n_out, seed, X.device)
     m = torch.zeros_like(params)
@@ -127,63 +161,122 @@ def train(spec, X, y, steps=1500, batch=64, lr=1e-3, seed=0):
 
 
 def propose(spec, model, feats, top=3):
-    """The `top` most probable (i1, i2, ir) grid candidates for each row of feats."""
+    """The `top` most probable (i1, i2, ir) grid candidates for each row of feats (ranked by the
+    library)."""
     n_out = sum(spec.heads)
-    logits = dp.dopinf_mlp_forward(model["params"], n_out, _standardise(feats, model["mu"], model["sd"]))
-    L = logits.cpu().numpy().astype(np.float64)   # a few numbers per system: ranked on the host
-    h1, h2, h3 = spec.heads
-
-    def logsoftmax(z):
-        z = z - z.max(axis=1, keepdims=True)
-        return z - np.log(np.exp(z).sum(axis=1, keepdims=True))
-    lp1, lp2, lp3 = logsoftmax(L[:, :h1]), logsoftmax(L[:, h1:h1 + h2]), logsoftmax(L[:, h1 + h2:])
-    joint = lp1[:, :, None, None] + lp2[:, None, :, None] + lp3[:, None, None, :]
-    flat = joint.reshape(joint.shape[0], -1)
-    best = np.argsort(-flat, axis=1, kind="stable")[:, :top]
-    out = []
-    for row in best:
-        out.append([(int(c // (h2 * h3)), int((c // h3) % h2), int(c % h3)) for c in row])
-    return out
+    logits = dp.dopinf_mlp_forward(model["params"], n_out, dp.dopinf_mlp_standardize(feats, model["mu"], model["sd"]))
+    ranked, _ = dp.dopinf_mlp_rank(logits, spec.heads, top)
+    return [[tuple(int(x) for x in c) for c in row if c[0] >= 0] for row in ranked.cpu().numpy()]
 
 
-def evaluate(spec, model, seeds, ws, top=3):
-    """Proposal-with-fallback against the full grid search on held-out systems."""
+def validation_error(spec, w, k, Qn, red, O, r, ws):
+    """Largest relative 2-norm error, over the held-out instants k .. k_total - 1, between the ROM
+    (operators O of dimension r) rolled out from the training window's first reduced state and
+    lifted with Step V, and the held-out snapshots transformed with the training statistics."""
+    k_tot = w.k
+    traj, fin = dp.dopinf_rollout(O, red["Qhat"][:r, 0].contiguous(), k_tot, mode=spec.mode, dt=1.0)
+    if int(fin.item()) != 1:
+        return float("inf")
+    X = dp.dopinf_lift(red["Q"], red["Tr"][:, :r], traj[k:].t(), ws=ws)        # n x k_val, transformed
+    S = torch.from_numpy(np.ascontiguousarray(Qn[:, k:])).to(X.device)
+    var = torch.from_numpy(np.repeat(np.arange(w.n_vars), w.n_per_var)).to(X.device)
+    S = (S - red["mean"][:, None]) / red["scale"][var][:, None]
+    err = torch.linalg.vector_norm(X - S, dim=0) / torch.linalg.vector_norm(S, dim=0)
+    return float(err.max().item())
+
+
+def _learn_one(spec, Qh, r, b1, b2, k, ws):
+    return dp.dopinf_learn(Qh, [r], [b1], [b2], spec.steps_factor * k, mode=spec.mode, dt=1.0, ws=ws)
+
+
+def evaluate(spec, model, seeds, ws, top=3, workers=None):
+    """Proposal-with-fallback against the full grid search on held-out systems: the ratio of the
+    validation errors of the two selections, their training-error ratio, and the time and the
+    candidate evaluations each needs."""
     b1, b2 = spec.beta1s(), spec.beta2s()
+    n_grid = len(spec.r_list) * spec.n_b1 * spec.n_b2
     rows = []
-    for s in seeds:
-        w = system(spec, s)
-        lam, tr, Qh = reduced(spec, w, ws)
+    for s, w, k, Qn in generated(spec, seeds, workers):
+        red = reduced(spec, w, k, Qn, ws)
+        Qh = red["Qhat"]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        grid = grid_search(spec, Qh, w.k, ws)
+        grid = grid_search(spec, Qh, k, ws)
         torch.cuda.synchronize()
         t_grid = time.perf_counter() - t0
         if grid["best"] < 0:
             continue
         t0 = time.perf_counter()
-        f = dp.dopinf_proposal_features(lam, tr, Qh)
+        f = dp.dopinf_proposal_features(red["eigvals"], red["trace"], Qh)
         cands = propose(spec, model, f[None, :], top)[0]
         chosen, tries, fallback = None, 0, False
         for (i1, i2, ir) in cands:
             tries += 1
-            res = dp.dopinf_learn(Qh, [spec.r_list[ir]], [b1[i1]], [b2[i2]], spec.steps_factor * w.k,
-                                  mode=spec.mode, dt=1.0, ws=ws)
+            res = _learn_one(spec, Qh, spec.r_list[ir], b1[i1], b2[i2], k, ws)
             if res["best"] >= 0:
-                chosen = float(res["train_err"][0].item())
+                chosen = res
                 break
         if chosen is None:
             fallback = True
-            chosen = float(grid_search(spec, Qh, w.k, ws)["train_err"][grid["best"]].item())
+            chosen = grid_search(spec, Qh, k, ws)
         torch.cuda.synchronize()
         t_prop = time.perf_counter() - t0
-        g_err = float(grid["train_err"][grid["best"]].item())
-        n_grid = len(spec.r_list) * spec.n_b1 * spec.n_b2
-        rows.append(dict(seed=s, ratio=chosen / g_err, tries=tries, fallback=fallback, t_grid=t_grid,
-                         t_prop=t_prop, evals=tries + (n_grid if fallback else 0)))
+        pick = chosen["best"]
+        e_prop = float(chosen["train_err"][pick].item())
+        e_grid = float(grid["train_err"][grid["best"]].item())
+        v_prop = validation_error(spec, w, k, Qn, red, chosen["O"], chosen["r"], ws)
+        v_grid = validation_error(spec, w, k, Qn, red, grid["O"], grid["r"], ws)
+        rows.append(dict(seed=s, ratio=e_prop / e_grid, val_ratio=v_prop / v_grid, val_prop=v_prop, val_grid=v_grid,
+                         tries=tries, fallback=fallback, t_grid=t_grid, t_prop=t_prop,
+                         evals=tries + (n_grid if fallback else 0)))
     ratios = np.array([r["ratio"] for r in rows])
+    vr = np.array([r["val_ratio"] for r in rows])
     return dict(n=len(rows), median_error_ratio=float(np.median(ratios)),
+                median_validation_error_ratio=float(np.median(vr[np.isfinite(vr)])) if np.isfinite(vr).any() else None,
+                validation_within_1p5=float(np.mean(vr <= 1.5)),
                 within_1p5=float(np.mean(ratios <= 1.5)), fallback_rate=float(np.mean([r["fallback"] for r in rows])),
                 top1_valid=float(np.mean([r["tries"] == 1 and not r["fallback"] for r in rows])),
                 speedup=float(np.sum([r["t_grid"] for r in rows]) / np.sum([r["t_prop"] for r in rows])),
-                work_ratio=float(len(spec.r_list) * spec.n_b1 * spec.n_b2 / np.mean([r["evals"] for r in rows])),
+                work_ratio=float(n_grid / np.mean([r["evals"] for r in rows])),
                 rows=rows)
+
+
+def experiment(spec, n_train, n_eval, steps=1500, workers=None, seed0=0, eval_seed0=1_000_000):
+    """Train on n_train seeded systems, evaluate on n_eval held-out ones, against the untrained
+    network too; returns a summary dict."""
+    ws = dp.Workspace("cuda")
+    t0 = time.perf_counter()
+    X, y, kept = dataset(spec, range(seed0, seed0 + n_train), ws, workers)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model = train(spec, X, y, steps=steps)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    seeds = range(eval_seed0, eval_seed0 + n_eval)
+    res = evaluate(spec, model, seeds, ws, workers=workers)
+    base = evaluate(spec, train(spec, X, y, steps=1, lr=0.0), seeds, ws, workers=workers)
+    strip = lambda d: {k: v for k, v in d.items() if k != "rows"}
+    return dict(spec=dict(r_list=list(spec.r_list), grid=[spec.n_b1, spec.n_b2], r_true_range=list(spec.r_true_range),
+                          k_range=list(spec.k_range), n_per_var=spec.n_per_var, val_frac=spec.val_frac,
+                          steps_factor=spec.steps_factor),
+                n_train=n_train, n_labelled=int(X.shape[0]), n_eval=n_eval, labelling_s=t_data, training_s=t_train,
+                final_loss=model["losses"][-1], trained=strip(res), untrained=strip(base))
+
+
+def main():
+    p = argparse.ArgumentParser(description="learned (beta1, beta2, r) proposal: train and evaluate")
+    p.add_argument("--train", type=int, default=1000)
+    p.add_argument("--eval", type=int, default=200)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--r-true", default="5,30")
+    p.add_argument("--k", default="300,800")
+    p.add_argument("--r-list", default="5,10,15,20,30")
+    a = p.parse_args()
+    lo, hi = (int(x) for x in a.r_true.split(","))
+    klo, khi = (int(x) for x in a.k.split(","))
+    spec = ProposalSpec(r_list=tuple(int(x) for x in a.r_list.split(",")), r_true_range=(lo, hi), k_range=(klo, khi))
+    print(json.dumps(experiment(spec, a.train, a.eval, steps=a.steps)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -96,3 +96,28 @@ def test_training_fits_a_separable_problem(dp):
             first = float(loss.item())
     last = float(loss.item())
     assert last < 0.05 * first
+
+
+def test_feature_stats_standardise_and_ranking_vs_oracle(dp):
+    """The library's input statistics and standardisation, and its ranking of the grid candidates
+    by joint log-probability, against the oracle's definitions."""
+    from oracle import mlp_oracle as M
+    rng = np.random.default_rng(3)
+    X = (rng.standard_normal((300, 64)) * rng.uniform(0.1, 50, 64) + rng.uniform(-5, 5, 64)).astype(np.float32)
+    X[:, 7] = 2.5                                               # a constant feature: floored deviation
+    Xd = torch.from_numpy(X).cuda()
+    mu, sd = dp.dopinf_mlp_feature_stats(Xd)
+    rmu, rsd = M.feature_stats(X)
+    assert np.allclose(mu.cpu().numpy(), rmu, rtol=1e-13, atol=0)
+    assert np.allclose(sd.cpu().numpy(), rsd, rtol=1e-12, atol=0)
+    Xs = dp.dopinf_mlp_standardize(Xd, mu, sd).cpu().numpy()
+    ref = M.standardise(X, mu.cpu().numpy(), sd.cpu().numpy())     # the same statistics: the same FP32 bits
+    assert np.array_equal(Xs, ref)
+    for heads, top in [((8, 8, 5), 5), ((6, 6, 3), 12), ((2, 3, 1), 6), ((1, 1, 1), 3)]:
+        L = (rng.standard_normal((40, sum(heads))) * 3).astype(np.float32)
+        ranked, score = dp.dopinf_mlp_rank(torch.from_numpy(L).cuda(), heads, top)
+        idx, sc = M.rank_candidates(L, heads, min(top, int(np.prod(heads))))
+        n = idx.shape[1]
+        assert np.array_equal(ranked.cpu().numpy()[:, :n], idx)
+        assert np.allclose(score.cpu().numpy()[:, :n], sc, rtol=1e-13, atol=1e-13)
+        assert np.all(ranked.cpu().numpy()[:, n:] == -1)

@@ -93,3 +93,24 @@ def test_features_closed_forms():
         assert abs(f[52 + j]) < 1e-12
     assert np.all(f[36 + 4:52] == 0) and np.all(f[52 + 4:63] == 0)
     assert f[63] == math.log10(k)
+
+
+def test_feature_stats_and_standardise_by_hand():
+    X = np.array([[1.0, 10.0], [3.0, 10.0], [5.0, 10.0]])
+    mu, sd = M.feature_stats(X)
+    assert mu.tolist() == [3.0, 10.0]
+    assert sd.tolist() == [2.0, 1e-6]           # sample std (ddof = 1); a constant feature is floored
+    Xs = M.standardise(X, mu, sd)
+    assert Xs.dtype == np.float32 and Xs[:, 0].tolist() == [-1.0, 0.0, 1.0] and Xs[:, 1].tolist() == [0.0] * 3
+
+
+def test_rank_candidates_by_hand():
+    """Heads of sizes (2, 2, 1): joint log-probabilities are sums of the per-head log-softmaxes;
+    equal joint scores keep the lowest flat index first."""
+    logits = np.array([[0.0, np.log(3.0), 0.0, 0.0, 5.0]])   # p1 = (1/4, 3/4), p2 = (1/2, 1/2), p3 = (1)
+    idx, sc = M.rank_candidates(logits, (2, 2, 1), 4)
+    assert idx[0].tolist() == [[1, 0, 0], [1, 1, 0], [0, 0, 0], [0, 1, 0]]
+    assert np.allclose(np.exp(sc[0]), [3 / 8, 3 / 8, 1 / 8, 1 / 8], rtol=1e-14)
+    # the joint distribution sums to one over every candidate
+    idx, sc = M.rank_candidates(np.random.default_rng(0).standard_normal((3, 9)), (3, 4, 2), 24)
+    assert np.allclose(np.exp(sc).sum(axis=1), 1.0, rtol=1e-12)
