@@ -686,6 +686,27 @@ def main():
     gram_flops = w.n * w.k * (w.k + 1)
     gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
     modes = gram_modes_measure(dp, Q, last["D"], args.pipeline_gram, stage["gram"], ws) if rank == 0 else None
+    qr = None
+    if rank == 0 and not args.no_extras:
+        # the learn step with the QR solver of the regularised problems instead of the
+        # block-Schur Cholesky: time of the solves, and the selection against the default's
+        prev = dp.dopinf_tune_learn_solver(dp.SOLVE_QR)
+        try:
+            for _ in range(2):
+                rq = dp.dopinf_learn(last["red"]["Qhat"], list(w.r_list), b1, b2, w.n_steps, mode=mode,
+                                     dt=w.snap_dt, ws=ws)
+            eq, ec = rq["train_err"].cpu().numpy(), res["train_err"].cpu().numpy()
+            ok = np.isfinite(eq) & np.isfinite(ec)
+            qr = {"solves_ms": rq["stage_ms"]["solves"] + rq["stage_ms"]["normal_equations"],
+                  "cholesky_solves_ms": float(np.mean([lp["solves"] + lp["normal_equations"]
+                                                       for lp in ev["learn_parts"]])),
+                  "learn_ms": sum(rq["stage_ms"].values()), "best": rq["best"], "same_best": rq["best"] == res["best"],
+                  "valid": int((rq["status"] == 0).sum().item()),
+                  "max_rel_train_err_diff_valid": float(np.max(np.abs(eq[ok] - ec[ok]) / ec[ok])) if ok.any() else None}
+        except Exception as ex:
+            qr = {"error": str(ex)}
+        finally:
+            dp.dopinf_tune_learn_solver(prev)
     lift = None
     if rank == 0 and not args.no_extras:
         try:
@@ -918,7 +939,7 @@ def main():
                 "timing": "CUDA events on the launching stream around the timed steps; inputs larger than L2",
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq,
-                "learn_double_word_rollouts": dw_roll, "step_v_lift": lift, "paper_shape": paper,
+                "learn_double_word_rollouts": dw_roll, "learn_qr_solver": qr, "step_v_lift": lift, "paper_shape": paper,
                 "batched_learn": batched, "proposal": proposal}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -303,6 +303,19 @@ int dopinf_tune_rollout_rows(int rows);
  * resident); other values only query.  Returns the previous value.  Process-wide.  The
  * results do not depend on it. */
 int dopinf_tune_rollout_rows_large(int rows);
+/* Solver of the regularised problems of dopinf_learn / dopinf_learn_async:
+ * DOPINF_SOLVE_CHOLESKY (default): the normal equations G + diag(reg), by block elimination of
+ *   the quadratic unknowns shared across beta1 (see dopinf_learn);
+ * DOPINF_SOLVE_QR: without the normal equations, the least-squares solution of the stacked
+ *   system [Dhat; diag(sqrt(reg))] O^T = [Y; 0] by Householder reflections (one CTA per
+ *   candidate) and back substitution: the conditioning of the stacked matrix, the square root
+ *   of the normal equations', at several times the cost; operators up to d = 1024 (r <= 44;
+ *   DOPINF_E_UNSUPPORTED above).  A zero diagonal of R marks the candidate as status 1.
+ * The workspace query reflects the solver set when it is called.  Other values only query.
+ * Returns the previous value.  Process-wide. */
+#define DOPINF_SOLVE_CHOLESKY 0
+#define DOPINF_SOLVE_QR 1
+int dopinf_tune_learn_solver(int solver);
 /* Rollout arithmetic of dopinf_learn: DOPINF_ROLLOUT_FP64 (default, the paper's) or DOPINF_ROLLOUT_DW; other
  * values only query.  Returns the previous value.  Process-wide. */
 int dopinf_tune_rollout_arith(int arith);

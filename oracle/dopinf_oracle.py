@@ -37,7 +37,7 @@ from scipy.linalg import solve_triangular
 
 __all__ = [
     "transform", "gram", "eig_desc", "energy_rank", "projection", "qhat_sq",
-    "data_matrix", "normal_equations", "regulariser", "solve_cholesky", "solve_lu",
+    "data_matrix", "normal_equations", "regulariser", "solve_cholesky", "solve_lu", "solve_qr",
     "split_operators", "rom_step_discrete", "rom_rhs", "rk4_step", "rollout",
     "train_error", "growth_ratio", "learn", "reduce", "pipeline", "pod_basis_rows", "lift",
 ]
@@ -235,6 +235,23 @@ def solve_cholesky(G, B, reg):
 def solve_lu(G, B, reg):
     """The paper's own route: np.linalg.solve (LU) of the regularised normal equations."""
     return np.linalg.solve(G + np.diag(reg), B).T
+
+
+def solve_qr(Dhat, Y, reg):
+    """The regularised least-squares problem of eq. OpInf_reg without forming the normal
+    equations: min ||Dhat O^T - Y||^2 + ||diag(sqrt(reg)) O^T||^2 as the least-squares solution of
+    the stacked system [Dhat; diag(sqrt(reg))] O^T = [Y; 0], by a Householder QR (numpy) and a
+    triangular solve.  Returns (O (r x d), ok); ok is False when R has a zero diagonal entry."""
+    Dhat = np.asarray(Dhat, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    d = Dhat.shape[1]
+    A = np.vstack([Dhat, np.diag(np.sqrt(np.asarray(reg, dtype=np.float64)))])
+    b = np.vstack([Y, np.zeros((d, Y.shape[1]))])
+    Qm, R = np.linalg.qr(A, mode="reduced")
+    if np.any(np.diag(R) == 0) or not np.all(np.isfinite(R)):
+        return None, False
+    X = solve_triangular(R, Qm.T @ b, lower=False)
+    return X.T, True
 
 
 def split_operators(O, r):

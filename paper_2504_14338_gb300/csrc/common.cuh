@@ -114,6 +114,12 @@ struct SchurCand {  // one (r, beta1, beta2)
   double b1;
   int r, s, m, N, unit, cand;
 };
+// QR route of the same regularised problems (qr_solve.cu): the candidates [cand0, cand0 + n) of
+// one r, each from the stacked system [Dhat; diag(sqrt(reg))] in its own slice of `work`
+// (stride doubles, at least qr_solve_doubles(K, r)); writes O and the candidate's status.
+size_t qr_solve_doubles(int64_t K, int r);
+int qr_solve(const double* Dh, const double* Y, int64_t K, int r, const SchurUnit* units, const SchurCand* cands,
+             int cand0, int n, double* work, size_t stride, int* cand_status, cudaStream_t st);
 size_t schur_unit_doubles(int r);
 size_t schur_cand_doubles(int r);
 int schur_solve(const SchurUnit* units_dev, const SchurUnit* units_host, int n_units, const SchurCand* cands_dev,

@@ -112,6 +112,8 @@ struct LearnWs {
   RolloutCand* roll;
   double *mu, *denom, *invden, *Dh, *Y;
   double *G[kMaxR], *B[kMaxR], *E[kMaxR], *S[kMaxR], *O[kMaxR];
+  double* qr;          // QR solver: one stacked system per candidate of an r (reused across r)
+  size_t qr_stride;    // doubles per candidate slice
   size_t O_off[kMaxR];  // byte offset of O[i] in the workspace
   int r_stride;  // largest r of the list: stride of the per-r vectors (mu)
   int64_t k_stride;  // snapshots: stride of the per-r training-error denominators
@@ -119,6 +121,9 @@ struct LearnWs {
   void* tn;
   size_t tn_bytes, used;
 };
+
+int g_solver = DOPINF_SOLVE_CHOLESKY;  // tunable: solver of the regularised problems
+constexpr int kQrMaxD = 1024;          // widest operator the QR solver takes (one CTA per candidate)
 
 LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1, int n_b2) {
   const int n_pairs = n_b1 * n_b2;
@@ -160,6 +165,15 @@ LearnWs carve_learn(void* base, int64_t K, const int* r_list, int n_r, int n_b1,
   }
   w.tn_bytes = tb;
   w.tn = c.take<char>(tb);
+  w.qr = nullptr;
+  w.qr_stride = 0;
+  if (g_solver == DOPINF_SOLVE_QR) {
+    for (int i = 0; i < n_r; ++i) {
+      const size_t q = qr_solve_doubles(K, r_list[i]);
+      w.qr_stride = q > w.qr_stride ? q : w.qr_stride;
+    }
+    w.qr = c.take<double>(w.qr_stride * (size_t)n_pairs);
+  }
   w.used = c.used;
   return w;
 }
@@ -290,9 +304,11 @@ int learn_check(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const in
     if (!(beta2[i] >= 0.0)) return DOPINF_E_ARG;
   if (!ws || ws_bytes < dopinf_learn_workspace(r_max, k, r_list, n_r, n_b1, n_b2) || misaligned(ws))
     return DOPINF_E_ARG;
-  // rollouts: every r must fit one of the two kernels (r <= 92)
-  for (int i = 0; i < n_r; ++i)
+  // rollouts: every r must fit one of the two kernels (r <= 92); the QR solver: d <= 1024
+  for (int i = 0; i < n_r; ++i) {
     if (!rollout_supported(r_list[i]) || !rollout_shape(r_list[i])) return DOPINF_E_UNSUPPORTED;
+    if (g_solver == DOPINF_SOLVE_QR && dim_d(r_list[i]) > kQrMaxD) return DOPINF_E_UNSUPPORTED;
+  }
   return DOPINF_OK;
 }
 
@@ -335,14 +351,21 @@ int learn_launch(const double* Qhat, int r_max, int64_t k, int64_t ldqh, const i
     const unsigned blocks = (unsigned)((tot + LB - 1) / LB < 4096 ? (tot + LB - 1) / LB : 4096);
     build_features<<<blocks, LB, 0, st>>>(Qhat, ldqh, r, d, K, t0, mode, dt, w.Dh, w.Y);
     DOPINF_TRY(launch_status());
-    DOPINF_TRY(tn_product(w.Dh, K, w.Dh, K, DOPINF_F64, K, d, d, 1, 0, w.G[ir], d, w.tn, w.tn_bytes, st));
-    DOPINF_TRY(tn_product(w.Dh, K, w.Y, K, DOPINF_F64, K, d, r, 0, 0, w.B[ir], d, w.tn, w.tn_bytes, st));
+    if (g_solver == DOPINF_SOLVE_QR) {
+      // this r's candidates from the stacked systems, before the next r rebuilds Dhat
+      DOPINF_TRY(qr_solve(w.Dh, w.Y, K, r, w.units, w.cands, ir * n_pairs, n_pairs, w.qr, w.qr_stride, cand_status,
+                          st));
+    } else {
+      DOPINF_TRY(tn_product(w.Dh, K, w.Dh, K, DOPINF_F64, K, d, d, 1, 0, w.G[ir], d, w.tn, w.tn_bytes, st));
+      DOPINF_TRY(tn_product(w.Dh, K, w.Y, K, DOPINF_F64, K, d, r, 0, 0, w.B[ir], d, w.tn, w.tn_bytes, st));
+    }
     train_stats<<<1, LB, 0, st>>>(Qhat, ldqh, r, k, w.mu + (size_t)ir * w.r_stride, w.denom + ir,
                                   w.invden + (size_t)ir * w.k_stride);
     DOPINF_TRY(launch_status());
   }
   if (ev) DOPINF_CUDA(cudaEventRecord(ev[1], st));
-  DOPINF_TRY(schur_solve(w.units, un.data(), n_units, w.cands, n_cand, w.unit_fail, cand_status, st));
+  if (g_solver != DOPINF_SOLVE_QR)
+    DOPINF_TRY(schur_solve(w.units, un.data(), n_units, w.cands, n_cand, w.unit_fail, cand_status, st));
   if (ev) DOPINF_CUDA(cudaEventRecord(ev[2], st));
   RolloutBatch bt = {};
   bt.cands = w.roll;
@@ -446,6 +469,12 @@ DOPINF_API int dopinf_learn(const double* Qhat, int r_max, int64_t k, int64_t ld
 }
 
 DOPINF_API int dopinf_tune_rollout_rows_large(int rows) { return rollout_set_rows_big(rows); }
+
+DOPINF_API int dopinf_tune_learn_solver(int solver) {
+  const int prev = g_solver;
+  if (solver == DOPINF_SOLVE_CHOLESKY || solver == DOPINF_SOLVE_QR) g_solver = solver;
+  return prev;
+}
 
 DOPINF_API int dopinf_tune_rollout_rows(int rows) { return rollout_set_rows(rows); }
 

@@ -25,6 +25,7 @@ GRAM_FP64, GRAM_BF16X4, GRAM_OZAKI_FP64 = 0, 1, 2
 DISCRETE, CONTINUOUS_RK4 = 0, 1
 ROLLOUT_FP64, ROLLOUT_DW = 1, 2
 TEST_GRID_BARRIER, TEST_TENSOR_GRAM = 1, 2
+SOLVE_CHOLESKY, SOLVE_QR = 0, 1
 
 _c_i64 = ctypes.c_int64
 _c_p = ctypes.c_void_p
@@ -89,6 +90,7 @@ def _load():
         "dopinf_mlp_standardize": (ctypes.c_int, [_c_p, ctypes.c_int, _c_p, _c_p, _c_p, _c_p]),
         "dopinf_mlp_rank": (ctypes.c_int, [_c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _c_p, _c_p,
                                            _c_p]),
+        "dopinf_tune_learn_solver": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_gram_chunk": (_c_i64, [_c_i64]),
         "dopinf_test_expire_waits": (ctypes.c_int, [ctypes.c_int]),
         "dopinf_tune_rollout_rows_large": (ctypes.c_int, [ctypes.c_int]),
@@ -243,6 +245,12 @@ def dopinf_gram_async(Q, D, flags, mode=GRAM_FP64, accumulate=False, ws=None, st
 def dopinf_tune_gram_chunk(rows=0):
     """Sets (rows > 0) or queries the FP32 accumulation chunk of the split Gram; returns the previous value."""
     return int(lib.dopinf_tune_gram_chunk(int(rows)))
+
+
+def dopinf_tune_learn_solver(solver=-1):
+    """Sets (SOLVE_CHOLESKY, SOLVE_QR) or queries the solver of the regularised problems of
+    dopinf_learn; returns the previous value."""
+    return int(lib.dopinf_tune_learn_solver(int(solver)))
 
 
 def dopinf_test_expire_waits(which=-1):

@@ -506,6 +506,33 @@ def test_learn_vs_oracle(dp, mode, arith):
     assert ref["train_err"][best] <= ref["train_err"][ref["best"]] * (1 + 1e-6) + 1e-12
 
 
+@pytest.mark.parametrize("mode", ["discrete", "continuous"])
+def test_learn_qr_solver_vs_oracle(dp, mode):
+    """The QR route of the regularised problems (no normal equations): every candidate's
+    operators against the oracle at the conditioning tolerance, statuses and metrics against the
+    oracle's rollouts; and, where the problem is well conditioned, the operators against the
+    oracle's own QR solve to 1e-10."""
+    Qh = _reduced(r_fixed=6)
+    b1 = synth.logspace(-8, 2, 4)
+    b2 = synth.logspace(-8, 2, 4)
+    dt = synth.WORKLOADS["small"].snap_dt
+    prev = dp.dopinf_tune_learn_solver(dp.SOLVE_QR)
+    try:
+        res, checked = _learn_parity(dp, Qh, [4, 6], b1, b2, 400, mode, dt)
+    finally:
+        dp.dopinf_tune_learn_solver(prev)
+    assert checked["ops"] >= 24 and checked["roll"] >= 24
+    for c in range(len(res["operators"])):
+        r = [4, 6][c // 16]
+        bb1, bb2 = b1[(c % 16) // 4], b2[c % 4]
+        if min(bb1, bb2) < 1e-2:
+            continue
+        Dh, Y = O.learning_data(Qh, r, mode, dt)
+        Oq, ok = O.solve_qr(Dh, Y, O.regulariser(r, bb1, bb2))
+        Og = res["operators"][c].cpu().numpy()
+        assert ok and np.linalg.norm(Og - Oq) <= 1e-10 * np.linalg.norm(Oq), c
+
+
 _LARGE = {}
 
 

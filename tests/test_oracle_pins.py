@@ -401,3 +401,35 @@ def test_transform_std_scaling_closed_form():
     # equals numpy's population standard deviation of the centred block
     C = R - R.mean(axis=1, keepdims=True)
     assert np.allclose(s, [C[:250].std(), C[250:].std()], rtol=1e-13)
+
+
+def test_qr_solve_equals_normal_equations_and_lstsq():
+    """The QR route of the regularised problem: on a well-conditioned problem it equals the
+    Cholesky solution of the normal equations and numpy's lstsq of the stacked system; on an
+    ill-conditioned one (tiny beta, nearly dependent columns) its residual of the regularised
+    normal equations stays at the rounding level of the stacked matrix, not of its square."""
+    rng = np.random.default_rng(21)
+    Qh = rng.standard_normal((5, 80))
+    Dh, Y = O.learning_data(Qh, 5)
+    G, B = O.normal_equations(Dh, Y)
+    reg = O.regulariser(5, 1e-1, 1e-1)
+    Oq, ok = O.solve_qr(Dh, Y, reg)
+    Oc, _ = O.solve_cholesky(G, B, reg)
+    assert ok and np.allclose(Oq, Oc, rtol=1e-10, atol=1e-12)
+    A = np.vstack([Dh, np.diag(np.sqrt(reg))])
+    b = np.vstack([Y, np.zeros((Dh.shape[1], 5))])
+    assert np.allclose(Oq.T, np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-10, atol=1e-12)
+    # nearly collinear data: the stacked system's conditioning, not its square
+    Qh2 = Qh.copy()
+    Qh2[1] = Qh2[0] * (1 + 1e-7) + 1e-9 * rng.standard_normal(80)
+    Dh2, Y2 = O.learning_data(Qh2, 5)
+    reg2 = O.regulariser(5, 1e-12, 1e-12)
+    Oq2, ok2 = O.solve_qr(Dh2, Y2, reg2)
+    A2 = np.vstack([Dh2, np.diag(np.sqrt(reg2))])
+    b2 = np.vstack([Y2, np.zeros((Dh2.shape[1], 5))])
+    ref = np.linalg.lstsq(A2, b2, rcond=None)[0]
+    assert ok2
+    # the least-squares residual norm is the minimum: QR reaches it to rounding
+    r_qr = np.linalg.norm(A2 @ Oq2.T - b2)
+    r_ref = np.linalg.norm(A2 @ ref - b2)
+    assert r_qr <= r_ref * (1 + 1e-8) + 1e-12
