@@ -735,15 +735,21 @@ def main():
         h2d_gbs = host_raw.numel() * host_raw.element_size() / (min(up) / 1e3) / 1e9
         h2d_gbs_one = host_raw.numel() * host_raw.element_size() / (min(up1) / 1e3) / 1e9
         sp = StreamingPipeline(host_raw, offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt,
-                               gram_mode=pipe_mode, device=dev)
+                               gram_mode=pipe_mode, device=dev, record_times=True)
         sp.run([host_raw] * max(2, args.warmup))
         torch.cuda.synchronize()
         n_e2e = max(6, args.steps)
         if world > 1:
             dist.barrier()
+        first = sp.count
         s0 = time.perf_counter()
         outs = sp.run([host_raw] * n_e2e)
         e2e_s = (time.perf_counter() - s0) / n_e2e
+        # inside the timed run: each upload, each step's compute, and the wait of a step's
+        # compute for its upload after the previous step ended
+        tms = [sp.step_times(i) for i in range(first, sp.count)]
+        in_pipe = {"upload_ms": [round(t[0], 2) for t in tms], "compute_ms": [round(t[1], 2) for t in tms],
+                   "gap_ms": [round(t[2], 2) for t in tms[1:]]}
         if world > 1:
             tt = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -754,18 +760,27 @@ def main():
                       "(pinned host -> device, copy stream) overlapping step i's captured pipeline; every "
                       "step's results copied back to pinned host memory and read",
                "best_index": outs[-1]["best"], "flags": outs[-1]["flags"],
-               "h2d_gbs_alone": h2d_gbs, "h2d_gbs_alone_one_copy": h2d_gbs_one, "host_cpus": host_cpus}
+               "h2d_gbs_alone": h2d_gbs, "h2d_gbs_alone_one_copy": h2d_gbs_one, "host_cpus": host_cpus,
+               "in_pipeline": in_pipe}
         del sp, outs
         torch.cuda.empty_cache()
         # serial: copy, eager pipeline, read-back, one after the other
         torch.cuda.synchronize()
+        ser = []
         s0 = time.perf_counter()
         for _ in range(n_e2e):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
             upload(QT, host_raw)
+            e[1].record(stream)
             res2 = step()
+            e[2].record(stream)
             outs = [o.cpu() for o in (res2["train_err"], res2["status"], res2["O_best"])]
+            ser.append(e)
         torch.cuda.synchronize()
         e2e["serial_value"] = world / ((time.perf_counter() - s0) / n_e2e)
+        e2e["serial_upload_ms"] = [round(e[0].elapsed_time(e[1]), 2) for e in ser]
+        e2e["serial_compute_ms"] = [round(e[1].elapsed_time(e[2]), 2) for e in ser]
         # the out-of-core Gram: the raw matrix streamed from pinned host memory in 8 row blocks
         # (the upload of block c + 1 under the Gram of block c), as for a matrix beyond HBM
         if rank == 0 and not args.no_extras:

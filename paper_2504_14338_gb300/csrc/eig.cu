@@ -4,15 +4,15 @@
 //
 // Only the leading r_cap eigenpairs are formed (the paper notes that a partial eigensolve
 // suffices when r is known; the energy rule needs only trace(D) besides them):
-//  1. Householder reduction of D to tridiagonal form T = H^T D H, one reflector per column,
-//     three launches per column: reflector, symmetric matrix-vector product, rank-2 update.
-//  2. the r_cap largest eigenvalues of T by Sturm-count multisection, one warp per
-//     eigenvalue, 32 trial points per round;
+//  1. Householder reduction of D to tridiagonal form T = H^T D H, one reflector per column:
+//     one cooperative launch with one grid barrier per column, or three launches per column;
+//  2. the r_cap largest eigenvalues of T by Sturm-count multisection, one CTA of 8 warps per
+//     eigenvalue, 256 trial points per round;
 //  3. their eigenvectors by inverse iteration with the partially pivoted tridiagonal LU,
 //     re-orthogonalised (modified Gram-Schmidt, twice) against earlier vectors whose
 //     eigenvalues lie within 1e-3 ||T||;
-//  4. back-transformation by the stored reflectors, sign rule (largest-magnitude entry
-//     positive, lowest index on ties);
+//  4. back-transformation by the stored reflectors in blocks of 16 (compact WY form), sign
+//     rule (largest-magnitude entry positive, lowest index on ties);
 //  5. T_r and Qhat = T_r^T D with the FP64 TN product.
 // All arithmetic is FP64; every reduction has a fixed order.
 #include "common.cuh"
@@ -23,24 +23,34 @@ namespace dopinf {
 namespace {
 
 constexpr int EB = 256;  // threads per block for the reduction kernels
+// block-reduction scratch: the warp partials (up to 32), the result, three broadcast scalars
+constexpr int kShSlots = 36;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  // fixed-order tree: warp shuffles, then the warp partials in warp order
+  // fixed-order tree: a butterfly in every warp, then one over the warp partials in warp 0
+  // (lanes beyond the warp count add zeros), broadcast through sh[32].  FP64 additions issue
+  // slowly here, so the second level runs in one warp only.
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double s = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) s += sh[i];
-  return s;
+  if (w == 0) {
+    double s = l < nw ? sh[l] : 0.0;
+    int pw = 1;
+    while (pw < nw) pw <<= 1;
+    for (int o = pw >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) sh[32] = s;
+  }
+  __syncthreads();
+  return sh[32];
 }
 
 // Reflector of column j: x = A[j+1:k, j] -> (I - tau v v^T) x = beta e1 with v[0] = 1.
 // v overwrites A[j+1:k, j]; d[j] = A[j][j], e[j] = beta.
 __global__ void __launch_bounds__(EB) hh_gen(double* A, int64_t k, int64_t j, double* d, double* e, double* tau) {
-  __shared__ double sh[32];
+  __shared__ double sh[kShSlots];
   double* x = A + j * k;  // column j
   double part = 0.0;
   for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) part += x[i] * x[i];
@@ -88,7 +98,7 @@ __global__ void __launch_bounds__(EB) hh_symv(const double* A, int64_t k, int64_
 // order and updates a group of columns of A22 (full symmetric storage).
 constexpr int R2_COLS = 16;
 __global__ void __launch_bounds__(EB) hh_rank2(double* A, int64_t k, int64_t j, const double* tau, const double* p) {
-  __shared__ double sh[32];
+  __shared__ double sh[kShSlots];
   const double t = tau[j];
   if (t == 0.0) return;
   const int64_t m = k - j - 1;
@@ -177,23 +187,33 @@ __device__ bool grid_sync(GridBar* b, unsigned stall) {
 
 // Householder vector of the column held in x (absolute rows, entries j+1..k-1), in place:
 // x[j+1] = 1, x[j+2..] scaled; returns tau, beta through the references (as hh_gen).
+// The square root and the two divisions are formed by one thread and broadcast (the same
+// operations as hh_gen, so the same values).
 __device__ void reflector_inplace(double* x, int64_t k, int64_t j, double* sh, double& t, double& beta) {
   double part = 0.0;
   for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) part += x[i] * x[i];
   const double sigma2 = block_sum(part, sh);
-  const double x0 = x[j + 1];
-  double scal;
-  if (sigma2 == 0.0) {
-    t = 0.0;
-    beta = x0;
-    scal = 0.0;
-  } else {
-    const double nrm = sqrt(x0 * x0 + sigma2);
-    beta = x0 >= 0.0 ? -nrm : nrm;
-    t = (beta - x0) / beta;
-    scal = 1.0 / (x0 - beta);
+  if (threadIdx.x == 0) {
+    const double x0 = x[j + 1];
+    double tt, bb, sc;
+    if (sigma2 == 0.0) {
+      tt = 0.0;
+      bb = x0;
+      sc = 0.0;
+    } else {
+      const double nrm = sqrt(x0 * x0 + sigma2);
+      bb = x0 >= 0.0 ? -nrm : nrm;
+      tt = (bb - x0) / bb;
+      sc = 1.0 / (x0 - bb);
+    }
+    sh[33] = tt;
+    sh[34] = bb;
+    sh[35] = sc;
   }
   __syncthreads();
+  t = sh[33];
+  beta = sh[34];
+  const double scal = sh[35];
   if (t != 0.0)
     for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) x[i] *= scal;
   __syncthreads();
@@ -205,15 +225,17 @@ __device__ void reflector_inplace(double* x, int64_t k, int64_t j, double* sh, d
 // whole reduction (every CTA gets its share, one column per scheduler while they last).  With
 // `resident`, a CTA keeps its columns in shared memory (slot c div grid) and reads them there;
 // every update is also written through to A, where the next step's column and the reflectors
-// are read by everyone.
+// are read by everyone.  Per step, after the barrier, each CTA fetches p_{j+1} and column j+2
+// together (one round trip to L2), forms w_j = p_j + alpha_j v_j once (in place of p_j) and
+// the updated column and its reflector from them.
 __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, double* d, double* e, double* tau,
                                                       double* pg, GridBar* bar, int resident, unsigned stall) {
   extern __shared__ double smd[];
   double* vj = smd;          // v_j (rows j+1..k-1)
-  double* pj = smd + k;      // p_j
-  double* vn = smd + 2 * k;  // column j+1 after update j, then v_{j+1}
+  double* pj = smd + k;      // p_j, then w_j
+  double* vn = smd + 2 * k;  // column j+1 as update j-1 left it, after update j, then v_{j+1}
   double* own = smd + 3 * k; // resident: this CTA's columns
-  __shared__ double sh[32];
+  __shared__ double sh[kShSlots];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t grid = gridDim.x;
   if (resident) {
@@ -221,33 +243,26 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
       const double* src = A + (blockIdx.x + lc * grid) * k;
       for (int64_t r = threadIdx.x; r < k; r += blockDim.x) own[lc * k + r] = src[r];
     }
-    __syncthreads();
   }
+  for (int64_t r = threadIdx.x; r < k; r += blockDim.x) vn[r] = __ldcg(A + r);  // column 0
+  __syncthreads();
   double tj = 0.0;  // tau of the pending update (0: none)
   for (int64_t j = -1; j + 2 < k; ++j) {
-    // (a) the pending update of step j: alpha = -tau_j/2 (p_j . v_j), w = p + alpha v
-    double alpha = 0.0;
-    if (j >= 0 && tj != 0.0) {
+    const bool upd = j >= 0 && tj != 0.0;
+    const int64_t c1 = j + 1;
+    if (upd) {
+      // (a) the pending update of step j: alpha = -tau_j/2 (p_j . v_j), w = p + alpha v
       const int64_t m = k - j - 1;
       double part = 0.0;
       for (int64_t l = threadIdx.x; l < m; l += blockDim.x) part = fma(pj[j + 1 + l], vj[j + 1 + l], part);
-      alpha = -0.5 * tj * block_sum(part, sh);
+      const double alpha = -0.5 * tj * block_sum(part, sh);
+      for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) pj[r] = fma(alpha, vj[r], pj[r]);
+      __syncthreads();
+      // (b) column j+1 after update j, rows j+1..k-1
+      const double vc = vj[c1], wc = pj[c1];
+      for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) vn[r] = fma(-pj[r], vc, fma(-vj[r], wc, vn[r]));
+      __syncthreads();
     }
-    const bool upd = j >= 0 && tj != 0.0;
-    // (b) column j+1 after update j, rows j+1..k-1
-    const int64_t c1 = j + 1;
-    {
-      const double vc = upd ? vj[c1] : 0.0, wc = upd ? fma(alpha, vc, pj[c1]) : 0.0;
-      for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) {
-        double a = __ldcg(A + r + c1 * k);
-        if (upd) {
-          const double wr = fma(alpha, vj[r], pj[r]);
-          a = fma(-wr, vc, fma(-vj[r], wc, a));
-        }
-        vn[r] = a;
-      }
-    }
-    __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) d[c1] = vn[c1];
     // (c) the stored reflector of column j (nobody reads column j any more)
     if (blockIdx.x == 0 && j >= 0) {
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
         const int64_t r = k - 1;
         double a = __ldcg(A + r + r * k);
         if (upd) {
-          const double vc = vj[r], wc = fma(alpha, vc, pj[r]);
+          const double vc = vj[r], wc = pj[r];
           a = fma(-wc, vc, fma(-vj[r], wc, a));
         }
         d[r] = a;
@@ -284,14 +299,13 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
         if (c < r0) continue;
         double* col = A + c * k;
         double* cs = resident ? own + lc * k : col;
-        const double vc = upd ? vj[c] : 0.0, wc = upd ? fma(alpha, vc, pj[c]) : 0.0;
+        const double vc = upd ? vj[c] : 0.0, wc = upd ? pj[c] : 0.0;
         double s = 0.0;
         for (int64_t l = lane; l < k - r0; l += 32) {
           const int64_t r = r0 + l;
           double a = resident ? cs[r] : __ldcg(col + r);
           if (upd) {
-            const double wr = fma(alpha, vj[r], pj[r]);
-            a = fma(-wr, vc, fma(-vj[r], wc, a));
+            a = fma(-pj[r], vc, fma(-vj[r], wc, a));
             col[r] = a;
             if (resident) cs[r] = a;
           }
@@ -302,29 +316,22 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
       }
     }
     if (!grid_sync(bar, stall)) return;
-    // (e) p_{j+1} to shared memory, v_{j+1} becomes the pending reflector
-    for (int64_t r = c1 + 1 + threadIdx.x; r < k; r += blockDim.x) pj[r] = tn != 0.0 ? __ldcg(pg + r) : 0.0;
-    for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) vj[r] = vn[r];
+    // (e) v_{j+1} becomes the pending reflector; p_{j+1} and column j+2 (rows j+2..k-1, as
+    // update j left it) from global memory, both loads issued before either is stored
+    const double* cn = A + (c1 + 1) * k;
+    for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) {
+      const double v = vn[r];
+      const double pv = r > c1 && tn != 0.0 ? __ldcg(pg + r) : 0.0;
+      const double cv = r > c1 ? __ldcg(cn + r) : 0.0;
+      vj[r] = v;
+      if (r > c1) {
+        pj[r] = pv;
+        vn[r] = cv;
+      }
+    }
     tj = tn;
     __syncthreads();
   }
-}
-
-// Gershgorin interval and the pivot floor of the Sturm count.
-__device__ void tri_bounds(const double* d, const double* e, int64_t k, double& lo, double& hi, double& pivmin) {
-  lo = DBL_MAX;
-  hi = -DBL_MAX;
-  double emax2 = 0.0;
-  for (int64_t i = 0; i < k; ++i) {
-    const double el = i > 0 ? fabs(e[i - 1]) : 0.0, er = i + 1 < k ? fabs(e[i]) : 0.0;
-    lo = fmin(lo, d[i] - el - er);
-    hi = fmax(hi, d[i] + el + er);
-    if (i + 1 < k) emax2 = fmax(emax2, e[i] * e[i]);
-  }
-  pivmin = DBL_MIN * fmax(1.0, emax2);
-  const double w = fmax(fabs(lo), fabs(hi));
-  lo -= 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
-  hi += 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
 }
 
 // Number of eigenvalues of T below x, without a division: the signs of the leading principal
@@ -372,10 +379,13 @@ __device__ int64_t sturm_count_poly(const double* d, const double* e2, int64_t k
 
 // T scaled by an exact power of two 2^-E with max(|d_i|, |e_i|) in [1, 2) (nothing to scale for
 // T = 0): ds, es and e2s = es^2, and the factor 2^E in *sc.  Counts and bisection run on the
-// scaled matrix; its eigenvalues times 2^E are those of T exactly.
+// scaled matrix; its eigenvalues times 2^E are those of T exactly.  Then the Gershgorin
+// interval of the scaled matrix and the pivot floor of the Sturm count, bnd = {lo, hi, pivmin,
+// ||T||} (minima and maxima are exact, so the parallel reduction gives the serial loop's values).
 __global__ void __launch_bounds__(256) tri_prep(const double* d, const double* e, int64_t k, double* ds, double* es,
-                                                double* e2s, double* sc) {
+                                                double* e2s, double* sc, double* bnd) {
   __shared__ unsigned long long sh[256];
+  __shared__ double shl[256], shh[256], she[256];
   unsigned long long mb = 0;
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
     const unsigned long long a = (unsigned long long)__double_as_longlong(d[i]) & 0x7fffffffffffffffull;
@@ -404,37 +414,79 @@ __global__ void __launch_bounds__(256) tri_prep(const double* d, const double* e
     e2s[i] = v * v;
   }
   if (threadIdx.x == 0) *sc = pow2(ex / 2) * pow2(ex - ex / 2);
+  __syncthreads();
+  double lo = DBL_MAX, hi = -DBL_MAX, emax2 = 0.0;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
+    const double el = i > 0 ? fabs(es[i - 1]) : 0.0, er = i + 1 < k ? fabs(es[i]) : 0.0;
+    lo = fmin(lo, ds[i] - el - er);
+    hi = fmax(hi, ds[i] + el + er);
+    if (i + 1 < k) emax2 = fmax(emax2, es[i] * es[i]);
+  }
+  shl[threadIdx.x] = lo;
+  shh[threadIdx.x] = hi;
+  she[threadIdx.x] = emax2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)blockDim.x; ++i) {
+      lo = fmin(lo, shl[i]);
+      hi = fmax(hi, shh[i]);
+      emax2 = fmax(emax2, she[i]);
+    }
+    const double pivmin = DBL_MIN * fmax(1.0, emax2);
+    const double w = fmax(fabs(lo), fabs(hi));
+    lo -= 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
+    hi += 4.0 * DBL_EPSILON * w + 2.0 * pivmin;
+    bnd[0] = lo;
+    bnd[1] = hi;
+    bnd[2] = pivmin;
+    bnd[3] = fmax(fabs(lo), fabs(hi));
+  }
 }
 
-// One warp per wanted eigenvalue (index idx in descending order = ascending index k-1-idx) of the
-// scaled matrix (tri_prep).  Each round evaluates 32 interior points of [lo, hi] and keeps the
-// sub-interval that holds the eigenvalue: a 33-fold reduction per round.
-__global__ void tri_multisect(const double* d, const double* e, const double* e2, const double* sc, int64_t k,
-                              int r_cap, double* lam, double* tnorm) {
-  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+// One CTA of MS_W warps per wanted eigenvalue (index idx in descending order = ascending index
+// k-1-idx) of the scaled matrix (tri_prep).  Each round evaluates 32 MS_W interior points of
+// [lo, hi], one per thread, and keeps the sub-interval that holds the eigenvalue: a
+// (32 MS_W + 1)-fold reduction per round.  The count is a chain of dependent FP64 operations,
+// so two warps share each scheduler at little cost and a round takes about one count.
+constexpr int MS_W = 8;
+__global__ void __launch_bounds__(32 * MS_W) tri_multisect(const double* d, const double* e2, const double* sc,
+                                                           const double* bnd, int64_t k, int r_cap, double* lam,
+                                                           double* tnorm) {
+  __shared__ unsigned s_above[MS_W];
+  __shared__ double s_x[32 * MS_W];
+  const int idx = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5;
+  constexpr int np = 32 * MS_W;
   if (idx >= r_cap) return;
-  double lo, hi, pivmin;
-  tri_bounds(d, e, k, lo, hi, pivmin);
-  const double tn = fmax(fabs(lo), fabs(hi));
+  double lo = bnd[0], hi = bnd[1];
+  const double pivmin = bnd[2], tn = bnd[3];
   const double f = *sc;
-  if (idx == 0 && lane == 0) *tnorm = tn * f;
+  if (idx == 0 && t == 0) *tnorm = tn * f;
   const int64_t a = k - 1 - idx;  // ascending index
   for (int round = 0; round < 64; ++round) {
     const double width = hi - lo;
     if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_EPSILON * tn + 4.0 * pivmin) break;
-    const double x = lo + width * (double)(lane + 1) / 33.0;
+    const double x = lo + width * (double)(t + 1) / (double)(np + 1);
     const int64_t c = sturm_count_poly(d, e2, k, x);
     // the eigenvalue lies below x iff count(x) > a
     const unsigned above = __ballot_sync(0xffffffffu, c > a);
-    const int first = above ? __ffs(above) - 1 : 32;  // first trial point above the eigenvalue
-    const double nlo = first == 0 ? lo : __shfl_sync(0xffffffffu, x, first - 1 < 0 ? 0 : first - 1);
-    const double nhi = first == 32 ? hi : __shfl_sync(0xffffffffu, x, first > 31 ? 31 : first);
+    if ((t & 31) == 0) s_above[warp] = above;
+    s_x[t] = x;
+    __syncthreads();
+    int first = np;  // first trial point above the eigenvalue
+    for (int w = 0; w < MS_W; ++w)
+      if (s_above[w]) {
+        first = w * 32 + __ffs(s_above[w]) - 1;
+        break;
+      }
+    const double nlo = first == 0 ? lo : s_x[first - 1];
+    const double nhi = first == np ? hi : s_x[first];
+    __syncthreads();
     if (nlo == lo && nhi == hi) break;
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) lam[idx] = 0.5 * (lo + hi) * f;
+  if (t == 0) lam[idx] = 0.5 * (lo + hi) * f;
 }
 
 __device__ __forceinline__ double start_value(int64_t i, int j) {
@@ -554,7 +606,7 @@ __global__ void __launch_bounds__(32) tri_invit(const double* d, const double* e
 // Modified Gram-Schmidt (twice) of each vector against the earlier vectors of its cluster
 // (|lambda_i - lambda_j| <= 1e-3 ||T||), then normalisation.  One block, vectors in order.
 __global__ void __launch_bounds__(EB) tri_orth(int64_t k, int r_cap, const double* lam, const double* tnorm, double* Z) {
-  __shared__ double sh[32];
+  __shared__ double sh[kShSlots];
   const double tol = 1e-3 * (*tnorm);
 #define ZZ(i, j) Z[(size_t)(i) * r_cap + (j)]
   for (int j = 1; j < r_cap; ++j) {
@@ -579,24 +631,98 @@ __global__ void __launch_bounds__(EB) tri_orth(int64_t k, int r_cap, const doubl
 #undef ZZ
 }
 
-// U[:, j] = H_0 H_1 ... H_{k-3} z_j, then the sign rule and T_r = U_r Lambda^{-1/2}.
-// One block per eigenvector; the vector lives in shared memory.
-__global__ void __launch_bounds__(EB) hh_back(const double* A, int64_t k, int r_cap, const double* tau,
-                                              const double* lam, const double* Z, double* U, double* Tr) {
+// Back-transformation in blocks of NBW reflectors, in the compact WY form (Schreiber and Van
+// Loan, SIAM J. Sci. Stat. Comput. 10 (1989)): H_{j0} H_{j0+1} ... H_{j0+nb-1} = I - V T V^T,
+// V the block's reflectors (zero above their leading 1) and T upper triangular with
+// T_ii = tau_i and T[0:l, l] = -tau_l T[0:l, 0:l] V[:, 0:l]^T v_l.  T is formed once per block
+// (wy_gram, wy_tfactor); each eigenvector then takes z -= V (T (V^T z)) per block, NBW
+// independent dot products instead of NBW dependent ones.
+constexpr int NBW = 16;
+
+// G[b][i][l] = v_{j0+i} . v_{j0+l} for i < l: block b = blockIdx.x, column l = blockIdx.y, one
+// warp per product, over the rows where v_{j0+l} is nonzero (j0+l+1..k-1).
+__global__ void __launch_bounds__(EB) wy_gram(const double* A, int64_t k, int64_t nrefl, double* G) {
+  const int64_t j0 = (int64_t)blockIdx.x * NBW;
+  const int l = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (j0 + l >= nrefl) return;
+  const double* vl = A + (j0 + l) * k;
+  double* g = G + (size_t)blockIdx.x * NBW * NBW;
+  for (int i = warp; i < l; i += EB / 32) {
+    const double* vi = A + (j0 + i) * k;
+    double s = 0.0;
+    for (int64_t r = j0 + l + 1 + lane; r < k; r += 32) s = fma(vi[r], vl[r], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) g[i * NBW + l] = s;
+  }
+}
+
+// T of block b = blockIdx.x (one warp, lane i forms row i), written over G's block.
+__global__ void __launch_bounds__(32) wy_tfactor(const double* tau, int64_t nrefl, double* G) {
+  __shared__ double T[NBW][NBW];
+  const int64_t j0 = (int64_t)blockIdx.x * NBW;
+  const int nb = (int)(nrefl - j0 < NBW ? nrefl - j0 : NBW);
+  const int i = threadIdx.x;
+  double* g = G + (size_t)blockIdx.x * NBW * NBW;
+  if (i < NBW)
+    for (int c = 0; c < NBW; ++c) T[i][c] = 0.0;
+  __syncwarp();
+  for (int l = 0; l < nb; ++l) {
+    const double tl = tau[j0 + l];
+    double s = 0.0;
+    if (i < l)
+      for (int m = i; m < l; ++m) s = fma(T[i][m], g[m * NBW + l], s);
+    __syncwarp();
+    if (i < l) T[i][l] = -tl * s;
+    if (i == l) T[i][l] = tl;
+    __syncwarp();
+  }
+  if (i < NBW)
+    for (int c = 0; c < NBW; ++c) g[i * NBW + c] = T[i][c];
+}
+
+// U[:, j] = H_0 H_1 ... H_{k-3} z_j (nrefl = k - 2 reflectors, the last block first), then the
+// sign rule and T_r = U_r Lambda^{-1/2}.  One block per eigenvector; the vector lives in
+// shared memory.
+__global__ void __launch_bounds__(EB) hh_back(const double* A, int64_t k, int r_cap, int64_t nrefl,
+                                              const double* Tw, const double* lam, const double* Z, double* U,
+                                              double* Tr) {
   extern __shared__ double z[];
-  __shared__ double sh[32];
+  __shared__ double y[NBW], yt[NBW];
   __shared__ int s_arg;
   const int j = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) z[i] = Z[(size_t)i * r_cap + j];
   __syncthreads();
-  for (int64_t jj = k - 3; jj >= 0; --jj) {
-    const double t = tau[jj];
-    if (t == 0.0) continue;
-    const double* v = A + jj * k;  // v at rows jj+1..k-1, v[jj+1] = 1
-    double part = 0.0;
-    for (int64_t i = jj + 1 + threadIdx.x; i < k; i += blockDim.x) part = fma(v[i], z[i], part);
-    const double s = t * block_sum(part, sh);
-    for (int64_t i = jj + 1 + threadIdx.x; i < k; i += blockDim.x) z[i] = fma(-s, v[i], z[i]);
+  const int64_t nblk = nrefl > 0 ? (nrefl + NBW - 1) / NBW : 0;
+  for (int64_t b = nblk - 1; b >= 0; --b) {
+    const int64_t j0 = b * NBW;
+    const int nb = (int)(nrefl - j0 < NBW ? nrefl - j0 : NBW);
+    // y = V^T z
+    for (int i = warp; i < nb; i += EB / 32) {
+      const double* vi = A + (j0 + i) * k;
+      double s = 0.0;
+      for (int64_t r = j0 + i + 1 + lane; r < k; r += 32) s = fma(vi[r], z[r], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) y[i] = s;
+    }
+    __syncthreads();
+    // yt = T y
+    if (threadIdx.x < nb) {
+      const double* T = Tw + (size_t)b * NBW * NBW;
+      const int i = threadIdx.x;
+      double s = 0.0;
+      for (int m = i; m < nb; ++m) s = fma(T[i * NBW + m], y[m], s);
+      yt[i] = s;
+    }
+    __syncthreads();
+    // z -= V yt: row r meets the reflectors i with j0 + i + 1 <= r
+    for (int64_t r = j0 + 1 + threadIdx.x; r < k; r += blockDim.x) {
+      const int ilim = (int)(r - j0 < nb ? r - j0 : nb);
+      double acc = z[r];
+      for (int i = 0; i < ilim; ++i) acc = fma(-A[r + (j0 + i) * k], yt[i], acc);
+      z[r] = acc;
+    }
     __syncthreads();
   }
   // sign rule: the entry of largest magnitude is positive (lowest index on ties)
@@ -648,7 +774,7 @@ __global__ void finalize_rank(const double* D, int64_t k, int64_t ldd, const dou
 }
 
 struct ReduceWs {
-  double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *iv, *trace, *ds, *es, *e2s, *sc;
+  double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *iv, *trace, *ds, *es, *e2s, *sc, *bnd, *wy;
   int* r;
   GridBar* bar;
   void* tn;
@@ -676,6 +802,9 @@ ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
   w.es = c.take<double>(k);
   w.e2s = c.take<double>(k);
   w.sc = c.take<double>(1);
+  w.bnd = c.take<double>(4);
+  const int64_t nblk = k > 2 ? (k - 2 + NBW - 1) / NBW : 1;
+  w.wy = c.take<double>((size_t)nblk * NBW * NBW);  // the T factors of the back-transformation
   w.tn_bytes = tn_workspace(k, r_cap, k, 0);
   w.tn = c.take<char>(w.tn_bytes);
   w.used = c.used;
@@ -761,19 +890,25 @@ int reduce_launch(const double* D, int64_t k, int64_t ldd, double energy_target,
   DOPINF_CUDA(cudaMemcpy2DAsync(w.A, k * sizeof(double), D, ldd * sizeof(double), k * sizeof(double), k,
                                 cudaMemcpyDeviceToDevice, st));
   DOPINF_TRY(tridiagonalise(w, k, st));
-  // one eigenvalue (a warp) and one eigenvector (a thread) per CTA: both are chains of FP64
-  // divisions, so they are spread over the SMs rather than packed into a few warps
-  tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.ds, w.es, w.e2s, w.sc);
-  tri_multisect<<<r_cap, 32, 0, st>>>(w.ds, w.es, w.e2s, w.sc, k, r_cap, w.lam, w.tnorm);
+  // one eigenvalue (8 warps) and one eigenvector (a warp) per CTA: both are chains of dependent
+  // FP64 operations, so they are spread over the SMs rather than packed into a few
+  tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.ds, w.es, w.e2s, w.sc, w.bnd);
+  tri_multisect<<<r_cap, 32 * MS_W, 0, st>>>(w.ds, w.e2s, w.sc, w.bnd, k, r_cap, w.lam, w.tnorm);
   DOPINF_TRY(launch_status());
   const size_t iv_smem = k <= kInvitSmemK ? (size_t)k * (5 * sizeof(double) + 1) : 0;
   if (iv_smem > 48 * 1024)
     DOPINF_CUDA(cudaFuncSetAttribute(tri_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iv_smem));
   tri_invit<<<r_cap, 32, iv_smem, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.iv, w.Z);
   tri_orth<<<1, EB, 0, st>>>(k, r_cap, w.lam, w.tnorm, w.Z);
+  const int64_t nrefl = k > 2 ? k - 2 : 0;
+  if (nrefl > 0) {
+    const unsigned nblk = (unsigned)((nrefl + NBW - 1) / NBW);
+    wy_gram<<<dim3(nblk, NBW), EB, 0, st>>>(w.A, k, nrefl, w.wy);
+    wy_tfactor<<<nblk, 32, 0, st>>>(w.tau, nrefl, w.wy);
+  }
   const size_t smem = (size_t)k * sizeof(double);
   if (smem > 48 * 1024) DOPINF_CUDA(cudaFuncSetAttribute(hh_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  hh_back<<<r_cap, EB, smem, st>>>(w.A, k, r_cap, w.tau, w.lam, w.Z, w.U, Tr);
+  hh_back<<<r_cap, EB, smem, st>>>(w.A, k, r_cap, nrefl, w.wy, w.lam, w.Z, w.U, Tr);
   DOPINF_TRY(launch_status());
   DOPINF_TRY(tn_product(Tr, k, D, ldd, DOPINF_F64, k, r_cap, k, 0, 0, Qhat, r_cap, w.tn, w.tn_bytes, st));
   finalize_rank<<<1, 32, 0, st>>>(D, k, ldd, w.lam, r_cap, energy_target, r_fixed, eigvals, r_dev, trace_dev);

@@ -198,9 +198,11 @@ class StreamingPipeline:
 
     def __init__(self, host_QT, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE,
                  dt=1.0, gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2,
-                 device="cuda", upload_chunks=8):
+                 device="cuda", upload_chunks=8, record_times=False):
         """host_QT: pinned CPU tensor (k, n), row-major, i.e. the column-major n x k snapshot matrix;
-        every submitted matrix has this shape and dtype.  The first one also serves for capture."""
+        every submitted matrix has this shape and dtype.  The first one also serves for capture.
+        record_times: bracket every upload and every step's compute with timing events
+        (step_times(i) reads them), to see whether the uploads hide behind the compute."""
         if not host_QT.is_pinned():
             raise ValueError("host_QT must be in pinned host memory")
         dev = torch.device(device)
@@ -228,6 +230,7 @@ class StreamingPipeline:
         self.h2d_bytes = host_QT.numel() * host_QT.element_size()
         self.d2h_bytes = sum(t.numel() * t.element_size() for t in srcs)
         self.count = 0
+        self.times = {} if record_times else None
 
     def submit(self, host_QT):
         """Queue one step on host_QT (pinned, the shape of the first); returns its index.
@@ -238,15 +241,26 @@ class StreamingPipeline:
         i, b = self.count, self.count % 2
         pg = self.pg[b]
         # the upload into copy b waits for the front graph that last read it (step i - 2)
+        tm = None
+        if self.times is not None:
+            tm = self.times[i] = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         self.copy_stream.wait_event(self.front_done[b])
         with torch.cuda.stream(self.copy_stream):
+            if tm:
+                tm[0].record(self.copy_stream)
             upload(self.QT[b], host_QT, self.upload_chunks)
+            if tm:
+                tm[1].record(self.copy_stream)
             self.uploaded[b].record(self.copy_stream)
         self.stream.wait_event(self.uploaded[b])
         with torch.cuda.stream(self.stream):
+            if tm:
+                tm[2].record(self.stream)
             pg.replay_front()
             self.front_done[b].record(self.stream)
             self.pg[0].replay_back()
+            if tm:
+                tm[3].record(self.stream)
             srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
             for dst, src in zip(self.host_out[b], srcs):
                 dst.copy_(src, non_blocking=True)
@@ -261,6 +275,17 @@ class StreamingPipeline:
         if not (self.count - 2 <= i < self.count):
             raise ValueError("step %d is no longer (or not yet) held" % i)
         return self.uploaded[i % 2]
+
+    def step_times(self, i):
+        """(upload ms, compute ms, gap ms) of step i (waits for it; record_times=True): the gap
+        is the time from the end of step i - 1's compute to the start of step i's, nonzero where
+        the compute waited for the upload (None for step 0)."""
+        if self.times is None:
+            raise ValueError("constructed without record_times")
+        tm = self.times[i]
+        tm[3].synchronize()
+        gap = self.times[i - 1][3].elapsed_time(tm[2]) if i - 1 in self.times else None
+        return tm[0].elapsed_time(tm[1]), tm[2].elapsed_time(tm[3]), gap
 
     def result(self, i):
         """Step i's results on the host (waits for them); valid until step i + 2 is submitted."""
