@@ -236,7 +236,9 @@ int dopinf_gram_fp64_noalloc(const void* Q, int dtype, int64_t n, int64_t k, int
  *              The Qhat of any r <= r_cap is its leading r rows.
  * r_out, trace_out  host, the chosen r and trace(D).
  * Synchronises the stream (r is returned on the host).  Returns DOPINF_E_RANK if
- * lambda_r <= 0 or the energy target is not reached within r_cap.
+ * lambda_r <= 0 or the energy target is not reached within r_cap.  Limits: k <= 25600 and
+ * r_cap <= 8532 (the eigenvector and its re-orthogonalisation coefficients are kept in
+ * shared memory; DOPINF_E_UNSUPPORTED above).
  * Workspace: dopinf_reduce_workspace(k, r_cap) bytes.
  * ------------------------------------------------------------------------------------ */
 size_t dopinf_reduce_workspace(int64_t k, int r_cap);

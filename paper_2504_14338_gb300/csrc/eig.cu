@@ -16,6 +16,7 @@
 //  5. T_r and Qhat = T_r^T D with the FP64 TN product.
 // All arithmetic is FP64; every reduction has a fixed order.
 #include "common.cuh"
+#include <cooperative_groups.h>
 #include <math.h>
 #include <float.h>
 
@@ -47,14 +48,60 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
+// The sums of the tridiagonalisation run over the first RW = 128 threads (one warp per
+// scheduler: FP64 instructions issue slowly, and a warp pair on one scheduler would share its
+// pipe): thread t < RW adds the entries t, t + RW, ... in order, each of the four warps sums its
+// lanes by a butterfly, warp 0 adds the four warp sums by a butterfly, and the result is
+// broadcast through sh[32].  block_sum_lo is called by all threads of the block (the others
+// pass nothing and wait); block_sum_named by warps 0-3 only, which then synchronise among
+// themselves on named barrier 1 while the other warps work on.
+constexpr int RW = 128;
+__device__ __forceinline__ void bar_lo() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ double warp_pair_sum4(double* sh) {
+  const int l = threadIdx.x & 31;
+  double s = l < 4 ? sh[l] : 0.0;
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+__device__ __forceinline__ double block_sum_lo(double v, double* sh) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (w < 4) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) sh[w] = v;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const double s = warp_pair_sum4(sh);
+    if (l == 0) sh[32] = s;
+  }
+  __syncthreads();
+  return sh[32];
+}
+__device__ __forceinline__ double block_sum_named(double v, double* sh) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  bar_lo();
+  if (l == 0) sh[w] = v;
+  bar_lo();
+  if (w == 0) {
+    const double s = warp_pair_sum4(sh);
+    if (l == 0) sh[32] = s;
+  }
+  bar_lo();
+  return sh[32];
+}
+
 // Reflector of column j: x = A[j+1:k, j] -> (I - tau v v^T) x = beta e1 with v[0] = 1.
 // v overwrites A[j+1:k, j]; d[j] = A[j][j], e[j] = beta.
 __global__ void __launch_bounds__(EB) hh_gen(double* A, int64_t k, int64_t j, double* d, double* e, double* tau) {
   __shared__ double sh[kShSlots];
   double* x = A + j * k;  // column j
   double part = 0.0;
-  for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) part += x[i] * x[i];
-  const double sigma2 = block_sum(part, sh);
+  if (threadIdx.x < RW)
+    for (int64_t i = j + 2 + threadIdx.x; i < k; i += RW) part += x[i] * x[i];
+  const double sigma2 = block_sum_lo(part, sh);
   const double x0 = x[j + 1];
   double t, beta, scal;
   if (sigma2 == 0.0) {
@@ -104,8 +151,9 @@ __global__ void __launch_bounds__(EB) hh_rank2(double* A, int64_t k, int64_t j, 
   const int64_t m = k - j - 1;
   const double* v = A + j * k + (j + 1);
   double part = 0.0;
-  for (int64_t l = threadIdx.x; l < m; l += blockDim.x) part = fma(p[l], v[l], part);
-  const double alpha = -0.5 * t * block_sum(part, sh);
+  if (threadIdx.x < RW)
+    for (int64_t l = threadIdx.x; l < m; l += RW) part = fma(p[l], v[l], part);
+  const double alpha = -0.5 * t * block_sum_lo(part, sh);
   const int64_t c0 = (int64_t)blockIdx.x * R2_COLS;
   for (int cc = 0; cc < R2_COLS; ++cc) {
     const int64_t c = c0 + cc;
@@ -132,18 +180,18 @@ __global__ void hh_tail(const double* A, int64_t k, double* d, double* e, double
 }
 
 // ---------------------------------------------------------------------------------------
-// The same reduction in one cooperative launch.  The rank-2 update of step j is applied by
-// the warp that also forms row c of the next product p_{j+1} = tau_{j+1} A22 v_{j+1} (the
-// matrix is symmetric, so row c is column c): each trailing column is read and written once
-// per step, and one grid barrier per column separates the steps.  Every CTA forms the next
-// reflector redundantly from its own copy of the updated column j+1, with the reductions in
-// the same fixed order as the three-launch version, so the results agree bit for bit.
-// The barrier is a counter and a generation word with a bounded wait: on expiry the kernel
-// sets an error word and every CTA returns.
+// The same reduction in one cooperative launch.  The rank-2 update of step j and the row c of
+// the next product p_{j+1} = tau_{j+1} A22 v_{j+1} (the matrix is symmetric, so row c is
+// column c) are formed by the CTA that owns column c, and one grid barrier per column
+// separates the steps.  Every CTA forms the next reflector redundantly from its own copy of
+// the updated column j+1, with the reductions in the same fixed order as the three-launch
+// version, so the results agree bit for bit.
+// The barrier is a counter with a bounded wait: on expiry the kernel sets an error word and
+// every CTA returns.
 constexpr int TB = 256;
 constexpr uint64_t kBarNs = 2000000000ull;
 struct GridBar {
-  unsigned count, gen, err;
+  unsigned count, err;
 };
 
 __device__ __forceinline__ uint64_t gtimer_ns() {
@@ -152,23 +200,22 @@ __device__ __forceinline__ uint64_t gtimer_ns() {
   return t;
 }
 
-// stall = 1 (a test of the error path) withholds the release: the arrivals can never reach
-// the count it waits for, so every wait runs into its limit.
-__device__ bool grid_sync(GridBar* b, unsigned stall) {
+// Arrival is one add on a counter that only grows (zeroed before the launch): the barrier of
+// step s is passed once it reaches (s + 1) x grid, so the last arrival's add is all the others
+// wait for.  stall = 1 (a test of the error path) raises every target by one: the count can
+// never reach it, so every wait runs into its limit.
+__device__ bool grid_sync(GridBar* b, unsigned& epoch, unsigned stall) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &b->gen;
-    volatile unsigned* verr = &b->err;
-    const unsigned g = *vgen;
+    const unsigned target = (++epoch) * gridDim.x + stall;
     __threadfence();
-    if (atomicAdd(&b->count, 1u) == gridDim.x - 1 + stall) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
+    const unsigned prev = atomicAdd(&b->count, 1u);
+    if (prev + 1u != target) {
+      volatile unsigned* vcount = &b->count;
+      volatile unsigned* verr = &b->err;
       const uint64_t t0 = gtimer_ns();
-      while (*vgen == g) {
+      while ((int)(*vcount - target) < 0) {
         if (*verr) {
           ok = 0;
           break;
@@ -185,49 +232,14 @@ __device__ bool grid_sync(GridBar* b, unsigned stall) {
   return __syncthreads_and(ok) != 0;
 }
 
-// Householder vector of the column held in x (absolute rows, entries j+1..k-1), in place:
-// x[j+1] = 1, x[j+2..] scaled; returns tau, beta through the references (as hh_gen).
-// The square root and the two divisions are formed by one thread and broadcast (the same
-// operations as hh_gen, so the same values).
-__device__ void reflector_inplace(double* x, int64_t k, int64_t j, double* sh, double& t, double& beta) {
-  double part = 0.0;
-  for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) part += x[i] * x[i];
-  const double sigma2 = block_sum(part, sh);
-  if (threadIdx.x == 0) {
-    const double x0 = x[j + 1];
-    double tt, bb, sc;
-    if (sigma2 == 0.0) {
-      tt = 0.0;
-      bb = x0;
-      sc = 0.0;
-    } else {
-      const double nrm = sqrt(x0 * x0 + sigma2);
-      bb = x0 >= 0.0 ? -nrm : nrm;
-      tt = (bb - x0) / bb;
-      sc = 1.0 / (x0 - bb);
-    }
-    sh[33] = tt;
-    sh[34] = bb;
-    sh[35] = sc;
-  }
-  __syncthreads();
-  t = sh[33];
-  beta = sh[34];
-  const double scal = sh[35];
-  if (t != 0.0)
-    for (int64_t i = j + 2 + threadIdx.x; i < k; i += blockDim.x) x[i] *= scal;
-  __syncthreads();
-  if (threadIdx.x == 0) x[j + 1] = 1.0;
-  __syncthreads();
-}
-
-// Column c of the trailing matrix belongs to CTA c mod grid, warp (c div grid) mod 8, for the
-// whole reduction (every CTA gets its share, one column per scheduler while they last).  With
-// `resident`, a CTA keeps its columns in shared memory (slot c div grid) and reads them there;
-// every update is also written through to A, where the next step's column and the reflectors
-// are read by everyone.  Per step, after the barrier, each CTA fetches p_{j+1} and column j+2
-// together (one round trip to L2), forms w_j = p_j + alpha_j v_j once (in place of p_j) and
-// the updated column and its reflector from them.
+// Column c of the trailing matrix belongs to CTA c mod grid and is handled by warp
+// 4 + (c div grid) mod 4 for the whole reduction.  With `resident`, a CTA keeps its columns in
+// shared memory (slot c div grid) and writes to A only the columns that another CTA reads there
+// (the next column, and the last one for the final 2 x 2 block); without, the columns live in A.
+// Per step, after the barrier, each CTA fetches p_{j+1} and column j+2 together (one round
+// trip to L2), forms w_j = p_j + alpha_j v_j once (in place of p_j) and the updated column
+// j+1.  Then warps 0-3 form the reflector of that column while warps 4-7 apply update j to the
+// CTA's trailing columns, and warps 4-7 form the CTA's entries of p_{j+1} = tau A22 v_{j+1}.
 __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, double* d, double* e, double* tau,
                                                       double* pg, GridBar* bar, int resident, unsigned stall) {
   extern __shared__ double smd[];
@@ -247,6 +259,7 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
   for (int64_t r = threadIdx.x; r < k; r += blockDim.x) vn[r] = __ldcg(A + r);  // column 0
   __syncthreads();
   double tj = 0.0;  // tau of the pending update (0: none)
+  unsigned epoch = 0;
   for (int64_t j = -1; j + 2 < k; ++j) {
     const bool upd = j >= 0 && tj != 0.0;
     const int64_t c1 = j + 1;
@@ -254,8 +267,9 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
       // (a) the pending update of step j: alpha = -tau_j/2 (p_j . v_j), w = p + alpha v
       const int64_t m = k - j - 1;
       double part = 0.0;
-      for (int64_t l = threadIdx.x; l < m; l += blockDim.x) part = fma(pj[j + 1 + l], vj[j + 1 + l], part);
-      const double alpha = -0.5 * tj * block_sum(part, sh);
+      if (threadIdx.x < RW)
+        for (int64_t l = threadIdx.x; l < m; l += RW) part = fma(pj[j + 1 + l], vj[j + 1 + l], part);
+      const double alpha = -0.5 * tj * block_sum_lo(part, sh);
       for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) pj[r] = fma(alpha, vj[r], pj[r]);
       __syncthreads();
       // (b) column j+1 after update j, rows j+1..k-1
@@ -285,38 +299,76 @@ __global__ void __launch_bounds__(TB) hh_tridiag_coop(double* A, int64_t k, doub
       }
       return;
     }
-    double tn, beta;
-    reflector_inplace(vn, k, c1, sh, tn, beta);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      e[c1] = beta;
-      tau[c1] = tn;
-    }
-    // (d) update j on the trailing columns c >= j+2 (rows >= j+2), fused with p_{j+1}[c]
-    if (tn != 0.0 || upd) {
-      const int64_t r0 = c1 + 1;
-      for (int64_t lc = warp; blockIdx.x + lc * grid < k; lc += TB / 32) {
+    const int64_t r0 = c1 + 1;
+    if (warp < 4) {
+      // (d) the reflector of column j+1 in place in vn (rows j+2..k-1, vn[j+2] = 1), the
+      // scalars by threads 0 (tau, beta) and 32 (the scale) side by side
+      double part = 0.0;
+      for (int64_t i = c1 + 2 + threadIdx.x; i < k; i += RW) part += vn[i] * vn[i];
+      const double sigma2 = block_sum_named(part, sh);
+      if (threadIdx.x == 0 || threadIdx.x == 32) {
+        const double x0 = vn[r0];
+        double bb = x0, q = 0.0;
+        if (sigma2 != 0.0) {
+          const double nrm = sqrt(x0 * x0 + sigma2);
+          bb = x0 >= 0.0 ? -nrm : nrm;
+          q = threadIdx.x == 0 ? (bb - x0) / bb : 1.0 / (x0 - bb);
+        }
+        if (threadIdx.x == 0) {
+          sh[33] = q;
+          sh[34] = bb;
+        } else {
+          sh[35] = q;
+        }
+      }
+      bar_lo();
+      if (sh[33] != 0.0) {
+        const double scal = sh[35];
+        for (int64_t i = c1 + 2 + threadIdx.x; i < k; i += RW) vn[i] *= scal;
+      }
+      bar_lo();
+      if (threadIdx.x == 0) vn[r0] = 1.0;
+    } else if (upd) {
+      // (e) update j on the trailing columns c >= j+2 (rows >= j+2)
+      for (int64_t lc = warp - 4; blockIdx.x + lc * grid < k; lc += 4) {
         const int64_t c = blockIdx.x + lc * grid;
         if (c < r0) continue;
         double* col = A + c * k;
         double* cs = resident ? own + lc * k : col;
-        const double vc = upd ? vj[c] : 0.0, wc = upd ? pj[c] : 0.0;
-        double s = 0.0;
+        const bool through = !resident || c == r0 || c == k - 1;
+        const double vc = vj[c], wc = pj[c];
         for (int64_t l = lane; l < k - r0; l += 32) {
           const int64_t r = r0 + l;
           double a = resident ? cs[r] : __ldcg(col + r);
-          if (upd) {
-            a = fma(-pj[r], vc, fma(-vj[r], wc, a));
-            col[r] = a;
-            if (resident) cs[r] = a;
-          }
-          s = fma(a, vn[r], s);
+          a = fma(-pj[r], vc, fma(-vj[r], wc, a));
+          if (resident) cs[r] = a;
+          if (through) col[r] = a;
+        }
+      }
+    }
+    __syncthreads();
+    const double tn = sh[33];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      e[c1] = sh[34];
+      tau[c1] = tn;
+    }
+    // (f) this CTA's entries of p_{j+1} (warps 4-7, one column per warp at a time)
+    if (warp >= 4 && tn != 0.0) {
+      for (int64_t lc = warp - 4; blockIdx.x + lc * grid < k; lc += 4) {
+        const int64_t c = blockIdx.x + lc * grid;
+        if (c < r0) continue;
+        const double* cs = resident ? own + lc * k : A + c * k;
+        double s = 0.0;
+        for (int64_t l = lane; l < k - r0; l += 32) {
+          const int64_t r = r0 + l;
+          s = fma(resident ? cs[r] : __ldcg(cs + r), vn[r], s);
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) pg[c] = tn * s;
       }
     }
-    if (!grid_sync(bar, stall)) return;
-    // (e) v_{j+1} becomes the pending reflector; p_{j+1} and column j+2 (rows j+2..k-1, as
+    if (!grid_sync(bar, epoch, stall)) return;
+    // (g) v_{j+1} becomes the pending reflector; p_{j+1} and column j+2 (rows j+2..k-1, as
     // update j left it) from global memory, both loads issued before either is stored
     const double* cn = A + (c1 + 1) * k;
     for (int64_t r = c1 + threadIdx.x; r < k; r += blockDim.x) {
@@ -385,7 +437,7 @@ __device__ int64_t sturm_count_poly(const double* d, const double* e2, int64_t k
 __global__ void __launch_bounds__(256) tri_prep(const double* d, const double* e, int64_t k, double* ds, double* es,
                                                 double* e2s, double* sc, double* bnd) {
   __shared__ unsigned long long sh[256];
-  __shared__ double shl[256], shh[256], she[256];
+  __shared__ double shl[8], shh[8], she[8];
   unsigned long long mb = 0;
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
     const unsigned long long a = (unsigned long long)__double_as_longlong(d[i]) & 0x7fffffffffffffffull;
@@ -422,12 +474,19 @@ __global__ void __launch_bounds__(256) tri_prep(const double* d, const double* e
     hi = fmax(hi, ds[i] + el + er);
     if (i + 1 < k) emax2 = fmax(emax2, es[i] * es[i]);
   }
-  shl[threadIdx.x] = lo;
-  shh[threadIdx.x] = hi;
-  she[threadIdx.x] = emax2;
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    shl[threadIdx.x >> 5] = lo;
+    shh[threadIdx.x >> 5] = hi;
+    she[threadIdx.x >> 5] = emax2;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)blockDim.x; ++i) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
       lo = fmin(lo, shl[i]);
       hi = fmax(hi, shh[i]);
       emax2 = fmax(emax2, she[i]);
@@ -603,32 +662,74 @@ __global__ void __launch_bounds__(32) tri_invit(const double* d, const double* e
   for (int64_t i = lane; i < k; i += 32) Z[(size_t)i * r_cap + j] = z[i];
 }
 
-// Modified Gram-Schmidt (twice) of each vector against the earlier vectors of its cluster
-// (|lambda_i - lambda_j| <= 1e-3 ||T||), then normalisation.  One block, vectors in order.
+// Re-orthogonalisation of each vector against the earlier vectors of its group
+// (|lambda_i - lambda_j| <= 1e-3 ||T||), twice, then normalisation, on a cluster of OC CTAs:
+// CTA q owns rows [q k / OC, (q + 1) k / OC) of Z.  Classical Gram-Schmidt: the CTAs' partial
+// dot products of their rows land in shared memory; after a cluster barrier every CTA adds the
+// OC partials in rank order, so all apply the same coefficients to their own rows.  The
+// partials alternate between two buffers, so a buffer is rewritten only after a later barrier
+// that every reader of its previous contents has passed.  Vectors in order; the FP64 work is
+// spread over OC SMs.
+constexpr int OC = 8;
 __global__ void __launch_bounds__(EB) tri_orth(int64_t k, int r_cap, const double* lam, const double* tnorm, double* Z) {
+  extern __shared__ double orth_sm[];
+  double* part0 = orth_sm;                 // two buffers of r_cap + 1 partials
+  double* coef = orth_sm + 2 * (r_cap + 1);
   __shared__ double sh[kShSlots];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned q = cl.block_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = k * q / OC, r1 = k * (q + 1) / OC;
   const double tol = 1e-3 * (*tnorm);
+  int par = 0;
 #define ZZ(i, j) Z[(size_t)(i) * r_cap + (j)]
+  auto exchange = [&]() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  };
   for (int j = 1; j < r_cap; ++j) {
     int first = j;
     while (first > 0 && fabs(lam[first - 1] - lam[j]) <= tol) --first;
     if (first == j) continue;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int i = first; i < j; ++i) {
-        double part = 0.0;
-        for (int64_t r = threadIdx.x; r < k; r += blockDim.x) part = fma(ZZ(r, i), ZZ(r, j), part);
-        const double dot = block_sum(part, sh);
-        for (int64_t r = threadIdx.x; r < k; r += blockDim.x) ZZ(r, j) = ZZ(r, j) - dot * ZZ(r, i);
-        __syncthreads();
+      double* pp = part0 + par * (r_cap + 1);
+      for (int i = first + warp; i < j; i += EB / 32) {
+        double s = 0.0;
+        for (int64_t r = r0 + lane; r < r1; r += 32) s = fma(ZZ(r, i), ZZ(r, j), s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) pp[i] = s;
       }
+      exchange();
+      for (int i = first + threadIdx.x; i < j; i += blockDim.x) {
+        double c = 0.0;
+        for (unsigned o = 0; o < OC; ++o) c += cl.map_shared_rank(pp, o)[i];
+        coef[i] = c;
+      }
+      __syncthreads();
+      for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double z = ZZ(r, j);
+        for (int i = first; i < j; ++i) z = fma(-coef[i], ZZ(r, i), z);
+        ZZ(r, j) = z;
+      }
+      __syncthreads();
+      par ^= 1;
     }
+    double* pp = part0 + par * (r_cap + 1);
     double part = 0.0;
-    for (int64_t r = threadIdx.x; r < k; r += blockDim.x) part = fma(ZZ(r, j), ZZ(r, j), part);
-    const double inv = 1.0 / sqrt(block_sum(part, sh));
-    for (int64_t r = threadIdx.x; r < k; r += blockDim.x) ZZ(r, j) *= inv;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) part = fma(ZZ(r, j), ZZ(r, j), part);
+    const double nq = block_sum(part, sh);
+    if (threadIdx.x == 0) pp[r_cap] = nq;
+    exchange();
+    double nrm2 = 0.0;
+    for (unsigned o = 0; o < OC; ++o) nrm2 += cl.map_shared_rank(pp, o)[r_cap];
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) ZZ(r, j) *= inv;
     __syncthreads();
+    par ^= 1;
   }
 #undef ZZ
+  exchange();  // no CTA leaves while a peer may still read its shared memory
 }
 
 // Back-transformation in blocks of NBW reflectors, in the compact WY form (Schreiber and Van
@@ -749,11 +850,13 @@ __global__ void __launch_bounds__(EB) hh_back(const double* A, int64_t k, int r_
   }
 }
 
+// One warp: trace(D) as lane sums (lane l adds D_ii for i = l mod 32 in order) and a butterfly.
 __global__ void finalize_rank(const double* D, int64_t k, int64_t ldd, const double* lam, int r_cap, double tau,
                               int r_fixed, double* out_eig, int* r_dev, double* trace_dev) {
-  if (threadIdx.x != 0) return;
   double tr = 0.0;
-  for (int64_t i = 0; i < k; ++i) tr += D[i + i * ldd];
+  for (int64_t i = threadIdx.x; i < k; i += 32) tr += D[i + i * ldd];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if (threadIdx.x != 0) return;
   int r = 0;
   if (r_fixed > 0) {
     r = r_fixed;
@@ -883,6 +986,28 @@ __global__ void reduce_flags(const int* r, const unsigned* bar_err, unsigned* fl
   if (b) atomicOr(flags, b);
 }
 
+// The re-orthogonalisation as one cluster of OC CTAs; its shared memory holds 3 (r_cap + 1)
+// doubles (r_cap is at most k, and k is bounded by the back-transformation's shared memory).
+int launch_orth(int64_t k, int r_cap, const double* lam, const double* tnorm, double* Z, cudaStream_t st) {
+  const size_t smem = (size_t)3 * (r_cap + 1) * sizeof(double);
+  if (smem > 48 * 1024)
+    DOPINF_CUDA(cudaFuncSetAttribute(tri_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(OC, 1, 1);
+  cfg.blockDim = dim3(EB, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = OC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  DOPINF_CUDA(cudaLaunchKernelEx(&cfg, tri_orth, k, r_cap, lam, tnorm, Z));
+  return DOPINF_OK;
+}
+
 // Everything but the read-back: r and trace(D) land in r_dev / trace_dev (device).
 int reduce_launch(const double* D, int64_t k, int64_t ldd, double energy_target, int r_fixed, int r_cap,
                   int* r_dev, double* trace_dev, double* eigvals, double* Tr, double* Qhat, const ReduceWs& w,
@@ -899,7 +1024,7 @@ int reduce_launch(const double* D, int64_t k, int64_t ldd, double energy_target,
   if (iv_smem > 48 * 1024)
     DOPINF_CUDA(cudaFuncSetAttribute(tri_invit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)iv_smem));
   tri_invit<<<r_cap, 32, iv_smem, st>>>(w.d, w.e, k, r_cap, w.lam, w.tnorm, w.iv, w.Z);
-  tri_orth<<<1, EB, 0, st>>>(k, r_cap, w.lam, w.tnorm, w.Z);
+  DOPINF_TRY(launch_orth(k, r_cap, w.lam, w.tnorm, w.Z, st));
   const int64_t nrefl = k > 2 ? k - 2 : 0;
   if (nrefl > 0) {
     const unsigned nblk = (unsigned)((nrefl + NBW - 1) / NBW);
@@ -922,6 +1047,7 @@ int reduce_check(const double* D, int64_t k, int64_t ldd, double energy_target, 
   if (r_fixed <= 0 && !(energy_target >= 0.0 && energy_target < 1.0)) return DOPINF_E_ARG;
   if (!ws || ws_bytes < dopinf_reduce_workspace(k, r_cap) || misaligned(ws)) return DOPINF_E_ARG;
   if ((size_t)k * sizeof(double) > 200 * 1024) return DOPINF_E_UNSUPPORTED;  // back-transform keeps z in smem
+  if ((size_t)3 * (r_cap + 1) * sizeof(double) > 200 * 1024) return DOPINF_E_UNSUPPORTED;  // orthogonalisation
   return DOPINF_OK;
 }
 }  // namespace
