@@ -98,7 +98,7 @@ def reduced(spec, w, k, Qn, ws, device="cuda"):
     Q.copy_(torch.from_numpy(np.ascontiguousarray(Qn[:, :k])))
     mean, scale, _ = dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
     D = dp.dopinf_gram(Q, ws=ws)
-    r_cap = min(spec.r_cap, k - 1)
+    r_cap = min(max(spec.r_cap, max(spec.r_list)), k - 1)  # the grid's largest r needs its rows of Qhat
     red = dp.dopinf_reduce(D, r_cap=r_cap, r_fixed=r_cap, ws=ws)
     return dict(eigvals=red["eigvals"], trace=red["trace"], Qhat=red["Qhat"], Tr=red["Tr"], Q=Q, mean=mean,
                 scale=scale)
