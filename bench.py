@@ -44,8 +44,9 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--stage", default="all", choices=["all", "gram", "learn"],
-                   help="gram / learn: time only that stage (for profiling)")
+    p.add_argument("--stage", default="all", choices=["all", "gram", "reduce", "learn", "batched"],
+                   help="gram / reduce / learn: time only that stage (for profiling); batched: the batched-learn "
+                        "configuration alone")
     p.add_argument("--n-per-var", type=int, default=0, help="override rows per variable (smaller case)")
     p.add_argument("--no-split", action="store_true", help="skip the split-precision Gram measurement")
     p.add_argument("--gram-mode", default="fp64", choices=["fp64", "bf16x4", "ozaki"], help="Gram mode of --stage gram")
@@ -442,13 +443,16 @@ def lift_measure(dp, Q, offs, mean, scale, red, res, w, mode, reps=3):
     return out
 
 
-def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16):
-    """The batched learn configuration on a stated subset: n_problems of its 512 problems (r drawn
-    from U{10..80} with a fixed seed; reduced data of k = 1500 from step-flow-style generators,
+def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16, group=128, seq_problems=16):
+    """The batched learn configuration: the first n_problems of its 512 problems (r drawn from
+    U{10..80} with a fixed seed; reduced data of k = 1500 from step-flow-style generators,
     r_true = 40, each problem its own seed), each with the 16 x 16 grid and 10,000-step RK4
-    rollouts, all captured into one CUDA graph (one branch per problem) and replayed once.
-    Against it: the unbatched path, one candidate at a time (one dopinf_learn call each, no
-    graph), timed on n_sub of each problem's 256 candidates (the grid diagonal) and scaled to 256."""
+    rollouts.  Up to `group` problems are captured into one CUDA graph (one branch per problem)
+    and replayed once; larger sets run as several such graphs one after another (all 512 need
+    about 330 GB of workspace).  Against it: the unbatched path, one candidate at a time (one
+    dopinf_learn call each, no graph), timed on n_sub of the 256 candidates (the grid diagonal)
+    of up to seq_problems problems spread evenly over the set, and scaled to all candidates of
+    all problems."""
     import torch
     from paper_2504_14338_gb300.graph import BatchedLearnGraph
     rng = np.random.default_rng(20250417)
@@ -457,50 +461,62 @@ def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16):
     b1 = synth.logspace(-10.0, 0.0, 16)
     b2 = synth.logspace(-4.0, 4.0, 16)
     ws = dp.Workspace(dev)
-    problems = []
-    for p, r in enumerate(rs):
-        w = synth.Workload("batched-%d" % p, 2, 4000, 1500, 40, seed=30_000 + p)
-        Q = synth.snapshots_torch(w, dev).t()
-        dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
-        D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws)
-        red = dp.dopinf_reduce(D, r_cap=r, r_fixed=r, ws=ws)
-        problems.append(dict(Qhat=red["Qhat"].clone(memory_format=torch.preserve_format), r_list=[r], beta1=b1,
-                             beta2=b2))
-        del Q, D
     dt = 0.01
     n_steps = 10_000
-    bg = BatchedLearnGraph(problems, n_steps, mode=dp.CONTINUOUS_RK4, dt=dt).capture()
+    n_seq = min(seq_problems, n_problems)
+    seq_ids = sorted(set(int(i * n_problems // n_seq) for i in range(n_seq)))
+    seq_set = []
+    batched_ms, flops, valid, graphs = 0.0, 0, 0, 0
     stream = torch.cuda.current_stream()
-    e = _events(2)
-    e[0].record(stream)
-    bg.replay()
-    e[1].record(stream)
-    torch.cuda.synchronize()
-    batched_ms = e[0].elapsed_time(e[1])
-    flops, valid = 0, 0
-    for pr, out in zip(problems, bg.out):
-        r = pr["r_list"][0]
-        d = r + r * (r + 1) // 2 + 1
-        flops += int(out["steps"].sum().item()) * 4 * 2 * r * d
-        valid += int((out["status"] == 0).sum().item())
-    # the unbatched baseline on the grid diagonal of every problem
+    for g0 in range(0, n_problems, group):
+        problems = []
+        for p in range(g0, min(g0 + group, n_problems)):
+            r = rs[p]
+            w = synth.Workload("batched-%d" % p, 2, 4000, 1500, 40, seed=30_000 + p)
+            Q = synth.snapshots_torch(w, dev).t()
+            dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
+            D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws)
+            red = dp.dopinf_reduce(D, r_cap=r, r_fixed=r, ws=ws)
+            problems.append(dict(Qhat=red["Qhat"].clone(memory_format=torch.preserve_format), r_list=[r], beta1=b1,
+                                 beta2=b2))
+            if p in seq_ids:
+                seq_set.append(problems[-1])
+            del Q, D
+        bg = BatchedLearnGraph(problems, n_steps, mode=dp.CONTINUOUS_RK4, dt=dt).capture()
+        e = _events(2)
+        e[0].record(stream)
+        bg.replay()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        batched_ms += e[0].elapsed_time(e[1])
+        graphs += 1
+        for pr, out in zip(problems, bg.out):
+            r = pr["r_list"][0]
+            d = r + r * (r + 1) // 2 + 1
+            flops += int(out["steps"].sum().item()) * 4 * 2 * r * d
+            valid += int((out["status"] == 0).sum().item())
+        del bg, problems
+        torch.cuda.empty_cache()
+    # the unbatched baseline on the grid diagonal of the sampled problems
     t0 = time.perf_counter()
-    for pr in problems:
+    for pr in seq_set:
         for i in range(n_sub):
             j = i * 16 // n_sub
             dp.dopinf_learn(pr["Qhat"], pr["r_list"], [b1[j]], [b2[j]], n_steps, mode=dp.CONTINUOUS_RK4, dt=dt, ws=ws)
     torch.cuda.synchronize()
-    seq_ms = (time.perf_counter() - t0) * 1e3 * (256 / n_sub)
-    del bg
+    seq_ms = (time.perf_counter() - t0) * 1e3 * (256 / n_sub) * (n_problems / len(seq_set))
+    del seq_set
     torch.cuda.empty_cache()
-    return {"workload": "batched learn, %d of 512 problems: r=%s, 16x16 grid, k=1500, 10000-step RK4, f64, one graph"
-                        % (n_problems, rs),
+    shown = rs if n_problems <= 16 else "U{10..80}, first %d draws" % n_problems
+    return {"workload": "batched learn, %d of 512 problems: r=%s, 16x16 grid, k=1500, 10000-step RK4, f64, "
+                        "%d graph(s) of up to %d problems" % (n_problems, shown, graphs, group),
             "batched_ms": batched_ms, "problems_per_s": n_problems / (batched_ms / 1e3),
             "rollout_fp64_gflops": flops / (batched_ms / 1e3) / 1e9, "valid_candidates": valid,
             "n_candidates": 256 * n_problems,
             "sequential_ms_est": seq_ms, "speedup_vs_sequential": seq_ms / batched_ms,
-            "sequential_how": "one dopinf_learn call per candidate (no graph), timed on %d of each problem's 256 "
-                              "candidates (the grid diagonal), scaled x%.0f" % (n_sub, 256 / n_sub)}
+            "sequential_how": "one dopinf_learn call per candidate (no graph), timed on %d of the 256 candidates "
+                              "(the grid diagonal) of %d problems spread over the set, scaled x%.0f"
+                              % (n_sub, len(seq_ids), (256 / n_sub) * (n_problems / len(seq_ids)))}
 
 
 def sequential_learn_measure(dp, Qhat, w, mode):
@@ -578,6 +594,30 @@ def main():
         if rank == 0:
             print(json.dumps({"stage": "gram", "mode": args.gram_mode, "n": w.n, "k": w.k, "ms": ms,
                               "useful_tflops": w.n * w.k * (w.k + 1) / ms / 1e9}), flush=True)
+        return
+    if args.stage == "reduce":
+        # the eigensolve and projection of the workload's Gram (r_cap = the largest r)
+        dp.dopinf_transform(Q, offs, ws=ws)
+        D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws).clone()
+        r_cap = max(w.r_list)
+        times = []
+        for i in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            red = dp.dopinf_reduce(D, r_cap=r_cap, r_fixed=r_cap, ws=ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        if rank == 0:
+            print(json.dumps({"stage": "reduce", "k": w.k, "r_cap": r_cap, "ms": float(np.median(times)),
+                              "coop": dp.dopinf_tune_reduce_coop(-1)}), flush=True)
+        return
+    if args.stage == "batched":
+        # the batched-learn configuration alone (--batched-problems of its 512 problems)
+        out = batched_learn_measure(dp, synth, dev, n_problems=args.batched_problems)
+        if rank == 0:
+            print(json.dumps(dict(stage="batched", **out)), flush=True)
         return
     if args.stage == "learn":
         r_list = [int(x) for x in args.r_list.split(",")] if args.r_list else list(w.r_list)
@@ -683,6 +723,40 @@ def main():
                  "flags": pg.flags_value(), "best_index": int(pg.res["best"].item())}
         del pg
         torch.cuda.empty_cache()
+    # consecutive pipelines overlapped: step i + 1's transform and Gram (a second copy of the
+    # snapshot matrix, a second stream) beside step i's learn step; every step computes all of
+    # its stages
+    overlapped = None
+    if not args.no_graph:
+        from paper_2504_14338_gb300.graph import OverlappedPipeline
+        QT2 = QT.clone()
+        op = OverlappedPipeline([Q, QT2.t()], offs, r_max, w.r_list, b1, b2, w.n_steps, mode=mode, dt=w.snap_dt,
+                                gram_mode=pipe_mode)
+        for _ in range(max(2, args.warmup)):
+            op.submit()
+        op.join()
+        torch.cuda.synchronize()
+        clk2 = Clocks()
+        clk2.start()
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        op.start_after(stream)
+        for _ in range(args.steps):
+            op.submit()
+        op.join(stream)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        ck2 = clk2.stop()
+        oms = o0.elapsed_time(o1) / args.steps
+        last_out = op.results(op.count - 1)
+        overlapped = {"ms_per_step": oms, "value": world / (oms / 1e3), "unit": UNIT, "steps": args.steps,
+                      "flags": last_out["flags"], "best_index": int(last_out["res"]["best"].item()),
+                      "clocks": ck2,
+                      "how": "OverlappedPipeline: two device copies of the snapshot matrix; step i+1's transform and "
+                             "Gram on a second stream beside step i's learn step, the reduce alone; CUDA events "
+                             "around all steps"}
+        del op, QT2, last_out
+        torch.cuda.empty_cache()
     gram_flops = w.n * w.k * (w.k + 1)
     gram_tf = gram_flops / (stage["gram"] / 1e3) / 1e12
     modes = gram_modes_measure(dp, Q, last["D"], args.pipeline_gram, stage["gram"], ws) if rank == 0 else None
@@ -715,8 +789,8 @@ def main():
             lift = {"error": str(ex)}
 
     # e2e: host snapshot matrices (pinned) -> device, the pipeline through the C ABI, results
-    # back to pinned host memory every step.  Pipelined (the public StreamingPipeline): the
-    # upload of step i + 1 runs on a copy stream while step i's captured pipeline computes.
+    # back to pinned host memory every step.  Pipelined (the public StreamingPipeline): uploads
+    # on a copy stream, step i + 1's transform and Gram beside step i's learn step.
     # Serial, for reference: upload, then the eager pipeline, then the read-back.
     e2e = None
     if host_raw is not None:
@@ -745,20 +819,21 @@ def main():
         s0 = time.perf_counter()
         outs = sp.run([host_raw] * n_e2e)
         e2e_s = (time.perf_counter() - s0) / n_e2e
-        # inside the timed run: each upload, each step's compute, and the wait of a step's
-        # compute for its upload after the previous step ended
+        # inside the timed run: each upload, each step's span (transform start to learn end),
+        # and how long each step's input arrived after the previous step's reduce
         tms = [sp.step_times(i) for i in range(first, sp.count)]
-        in_pipe = {"upload_ms": [round(t[0], 2) for t in tms], "compute_ms": [round(t[1], 2) for t in tms],
-                   "gap_ms": [round(t[2], 2) for t in tms[1:]]}
+        in_pipe = {"upload_ms": [round(t[0], 2) for t in tms], "span_ms": [round(t[1], 2) for t in tms],
+                   "upload_wait_ms": [round(t[2], 2) for t in tms[1:]]}
         if world > 1:
             tt = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_s = float(tt.item())
         e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": sp.h2d_bytes,
                "d2h_bytes_per_step": sp.d2h_bytes, "ms_per_step": e2e_s * 1e3,
-               "how": "StreamingPipeline: two device copies of the snapshot matrix, the upload of step i+1 "
-                      "(pinned host -> device, copy stream) overlapping step i's captured pipeline; every "
-                      "step's results copied back to pinned host memory and read",
+               "how": "StreamingPipeline: two device copies of the snapshot matrix; uploads (pinned host -> "
+                      "device) on a copy stream, each step's transform and Gram beside the previous step's learn "
+                      "step, reduce and learn in turn; every step's results copied back to pinned host memory "
+                      "and read",
                "best_index": outs[-1]["best"], "flags": outs[-1]["flags"],
                "h2d_gbs_alone": h2d_gbs, "h2d_gbs_alone_one_copy": h2d_gbs_one, "host_cpus": host_cpus,
                "in_pipeline": in_pipe}
@@ -953,7 +1028,7 @@ def main():
                                             if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else "f64")},
                 "timing": "CUDA events on the launching stream around the timed steps; inputs larger than L2",
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
-                "clocks": ck, "autotune": tuned, "graph_replay": graph, "split_gram": split, "learn_vs_sequential": seq,
+                "clocks": ck, "autotune": tuned, "graph_replay": graph, "overlapped": overlapped, "split_gram": split, "learn_vs_sequential": seq,
                 "learn_double_word_rollouts": dw_roll, "learn_qr_solver": qr, "step_v_lift": lift, "paper_shape": paper,
                 "batched_learn": batched, "proposal": proposal}
         print(json.dumps(line), flush=True)

@@ -6,7 +6,8 @@
 // suffices when r is known; the energy rule needs only trace(D) besides them):
 //  1. Householder reduction of D to tridiagonal form T = H^T D H, one reflector per column:
 //     one cooperative launch with one grid barrier per column, or three launches per column;
-//  2. the r_cap largest eigenvalues of T by Sturm-count multisection, one CTA of 8 warps per
+//  2. the r_cap largest eigenvalues of T by Sturm-count multisection: a first round of 38912
+//     points shared by all eigenvalues over the whole GPU, then one CTA of 8 warps per
 //     eigenvalue, 256 trial points per round;
 //  3. their eigenvectors by inverse iteration with the partially pivoted tridiagonal LU,
 //     re-orthogonalised (modified Gram-Schmidt, twice) against earlier vectors whose
@@ -502,17 +503,32 @@ __global__ void __launch_bounds__(256) tri_prep(const double* d, const double* e
   }
 }
 
+// The first multisection round is shared by all eigenvalues: NGP points of the Gershgorin
+// interval [lo, hi] (x_t = lo + (hi - lo)(t + 1)/(NGP + 1)), one Sturm count per thread over the
+// whole GPU, about 15 bits of every eigenvalue in the time of one count.
+constexpr int NGP = 152 * 256;
+__global__ void __launch_bounds__(256) tri_count_grid(const double* d, const double* e2, const double* bnd, int64_t k,
+                                                      int* cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NGP) return;
+  const double lo = bnd[0], hi = bnd[1];
+  const double x = lo + (hi - lo) * (double)(t + 1) / (double)(NGP + 1);
+  cnt[t] = (int)sturm_count_poly(d, e2, k, x);
+}
+
 // One CTA of MS_W warps per wanted eigenvalue (index idx in descending order = ascending index
-// k-1-idx) of the scaled matrix (tri_prep).  Each round evaluates 32 MS_W interior points of
-// [lo, hi], one per thread, and keeps the sub-interval that holds the eigenvalue: a
-// (32 MS_W + 1)-fold reduction per round.  The count is a chain of dependent FP64 operations,
-// so two warps share each scheduler at little cost and a round takes about one count.
+// k-1-idx) of the scaled matrix (tri_prep).  It starts from the sub-interval the shared round
+// (tri_count_grid) left; each further round evaluates 32 MS_W interior points of [lo, hi], one
+// per thread, and keeps the sub-interval that holds the eigenvalue: a (32 MS_W + 1)-fold
+// reduction per round.  The count is a chain of dependent FP64 operations, so two warps share
+// each scheduler at little cost and a round takes about one count.
 constexpr int MS_W = 8;
 __global__ void __launch_bounds__(32 * MS_W) tri_multisect(const double* d, const double* e2, const double* sc,
-                                                           const double* bnd, int64_t k, int r_cap, double* lam,
-                                                           double* tnorm) {
+                                                           const double* bnd, const int* cnt, int64_t k, int r_cap,
+                                                           double* lam, double* tnorm) {
   __shared__ unsigned s_above[MS_W];
   __shared__ double s_x[32 * MS_W];
+  __shared__ int s_first;
   const int idx = blockIdx.x;
   const int t = threadIdx.x, warp = t >> 5;
   constexpr int np = 32 * MS_W;
@@ -522,6 +538,22 @@ __global__ void __launch_bounds__(32 * MS_W) tri_multisect(const double* d, cons
   const double f = *sc;
   if (idx == 0 && t == 0) *tnorm = tn * f;
   const int64_t a = k - 1 - idx;  // ascending index
+  {
+    // the shared round: the first of its points above the eigenvalue (count > a)
+    if (t == 0) s_first = NGP;
+    __syncthreads();
+    int first = NGP;  // independent loads, no early exit: the scan costs about one L2 round trip
+    for (int u = t; u < NGP; u += blockDim.x)
+      if (__ldg(cnt + u) > a && u < first) first = u;
+    if (first < NGP) atomicMin(&s_first, first);
+    __syncthreads();
+    const int g = s_first;
+    const double width = hi - lo;
+    const double nlo = g == 0 ? lo : lo + width * (double)g / (double)(NGP + 1);
+    const double nhi = g == NGP ? hi : lo + width * (double)(g + 1) / (double)(NGP + 1);
+    lo = nlo;
+    hi = nhi;
+  }
   for (int round = 0; round < 64; ++round) {
     const double width = hi - lo;
     if (width <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_EPSILON * tn + 4.0 * pivmin) break;
@@ -615,7 +647,12 @@ __global__ void __launch_bounds__(32) tri_invit(const double* d, const double* e
   for (int64_t i = lane; i < k; i += 32) {
     double g = Dg[i];
     if (fabs(g) < eps_piv) g = g < 0.0 ? -eps_piv : eps_piv;
-    Dg[i] = 1.0 / g;
+    const double rg = 1.0 / g;
+    Dg[i] = rg;
+    // the backward sweep's coefficients scaled by the reciprocal pivot, so that its dependent
+    // chain is one FMA per row: s_i = z_i/U_ii - (U_i,i+1/U_ii) s_{i+1} - (U_i,i+2/U_ii) s_{i+2}
+    Du[i] *= rg;
+    Du2[i] *= rg;
   }
   __syncwarp();
   for (int it = 0; it < 3; ++it) {
@@ -633,10 +670,11 @@ __global__ void __launch_bounds__(32) tri_invit(const double* d, const double* e
         }
       }
       z[k - 1] = zi;
-      // backward: U^{-1}, by the reciprocal pivots
+      // backward: U^{-1}, by the reciprocal pivots (the term of s_{i+2} is off the chain)
       double z1 = 0.0, z2 = 0.0;  // z[i + 1], z[i + 2]
       for (int64_t i = k - 1; i >= 0; --i) {
-        const double s = (z[i] - Du[i] * z1 - Du2[i] * z2) * Dg[i];
+        const double b = fma(-Du2[i], z2, z[i] * Dg[i]);
+        const double s = fma(-Du[i], z1, b);
         z[i] = s;
         z2 = z1;
         z1 = s;
@@ -878,7 +916,7 @@ __global__ void finalize_rank(const double* D, int64_t k, int64_t ldd, const dou
 
 struct ReduceWs {
   double *A, *d, *e, *tau, *p, *lam, *tnorm, *Z, *U, *iv, *trace, *ds, *es, *e2s, *sc, *bnd, *wy;
-  int* r;
+  int *r, *cnt;
   GridBar* bar;
   void* tn;
   size_t tn_bytes, used;
@@ -906,6 +944,7 @@ ReduceWs carve_reduce(void* base, int64_t k, int r_cap) {
   w.e2s = c.take<double>(k);
   w.sc = c.take<double>(1);
   w.bnd = c.take<double>(4);
+  w.cnt = c.take<int>(NGP);  // the counts of the shared multisection round
   const int64_t nblk = k > 2 ? (k - 2 + NBW - 1) / NBW : 1;
   w.wy = c.take<double>((size_t)nblk * NBW * NBW);  // the T factors of the back-transformation
   w.tn_bytes = tn_workspace(k, r_cap, k, 0);
@@ -1018,7 +1057,8 @@ int reduce_launch(const double* D, int64_t k, int64_t ldd, double energy_target,
   // one eigenvalue (8 warps) and one eigenvector (a warp) per CTA: both are chains of dependent
   // FP64 operations, so they are spread over the SMs rather than packed into a few
   tri_prep<<<1, 256, 0, st>>>(w.d, w.e, k, w.ds, w.es, w.e2s, w.sc, w.bnd);
-  tri_multisect<<<r_cap, 32 * MS_W, 0, st>>>(w.ds, w.e2s, w.sc, w.bnd, k, r_cap, w.lam, w.tnorm);
+  tri_count_grid<<<(NGP + 255) / 256, 256, 0, st>>>(w.ds, w.e2s, w.bnd, k, w.cnt);
+  tri_multisect<<<r_cap, 32 * MS_W, 0, st>>>(w.ds, w.e2s, w.sc, w.bnd, w.cnt, k, r_cap, w.lam, w.tnorm);
   DOPINF_TRY(launch_status());
   const size_t iv_smem = k <= kInvitSmemK ? (size_t)k * (5 * sizeof(double) + 1) : 0;
   if (iv_smem > 48 * 1024)

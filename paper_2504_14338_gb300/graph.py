@@ -18,9 +18,13 @@ from . import dopinf as dp
 
 class PipelineGraph:
     def __init__(self, Q, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0,
-                 gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2, share=None):
+                 gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2, share=None,
+                 share_back=None):
         """share: another PipelineGraph of the same sizes whose workspaces and output buffers
-        this one reuses (both graphs then run on one stream, one after the other)."""
+        this one reuses (both graphs then run on one stream, one after the other).
+        share_back: another PipelineGraph whose reduce and learn workspaces and outputs this one
+        reuses, with transform and Gram buffers (mean, scale, D, flags, their workspaces) of its
+        own: the front of one may then run beside the back of the other, the backs in turn."""
         self.Q = Q
         n, k, ldq = dp._colmajor(Q)
         dev = Q.device
@@ -44,10 +48,21 @@ class PipelineGraph:
             for name in ("flags", "mean", "scale", "D", "red", "res", "ws", "wbuf", "wsz"):
                 setattr(self, name, getattr(share, name))
             return
+        if share_back is not None:
+            if (share_back.k, share_back.r_cap, share_back.r_list) != (k, self.r_cap, self.r_list):
+                raise ValueError("share_back: the pipelines differ in size")
         self.flags = torch.zeros(1, dtype=i32, device=dev)
         self.mean = torch.empty(n, dtype=f64, device=dev)
         self.scale = torch.empty(self.n_vars, dtype=f64, device=dev)
         self.D = torch.zeros(k, k, dtype=f64, device=dev)
+        if share_back is not None:
+            self.red, self.res = share_back.red, share_back.res
+            sizes = [dp.lib.dopinf_transform_workspace(n, self.n_vars),
+                     dp.lib.dopinf_gram_workspace(n, k, dp._dtype_code(Q), gram_mode)]
+            self.ws = [dp.Workspace(dev) for _ in sizes] + share_back.ws[2:]
+            self.wbuf = [w.get(nb) for w, nb in zip(self.ws, sizes)] + share_back.wbuf[2:]
+            self.wsz = sizes + share_back.wsz[2:]
+            return
         self.red = dict(eigvals=torch.empty(r_cap, dtype=f64, device=dev),
                         Tr=torch.empty(r_cap, k, dtype=f64, device=dev).t(),
                         Qhat=torch.empty(k, r_cap, dtype=f64, device=dev).t(),
@@ -70,9 +85,10 @@ class PipelineGraph:
         self.wbuf = [w.get(nb) for w, nb in zip(self.ws, sizes)]
         self.wsz = sizes
 
-    def _launch(self, stream, front=True, back=True):
+    def _launch(self, stream, front=True, back=True, learn=True):
         """The pipeline on `stream` through the asynchronous entry points (no host synchronisation):
-        front = transform and Gram (the steps that read Q), back = reduce and learn."""
+        front = transform and Gram (the steps that read Q), back = reduce, then learn (unless
+        learn is False)."""
         L, P, s = dp.lib, dp._ptr, dp._stream(stream)
         red, res = self.red, self.res
         if front:
@@ -89,6 +105,13 @@ class PipelineGraph:
             P(self.D), self.k, self.D.stride(0), self.energy_target, self.r_fixed, self.r_cap, P(red["r"]),
             P(red["trace"]), P(red["eigvals"]), P(red["Tr"]), P(red["Qhat"]), P(self.flags), P(self.wbuf[2]),
             self.wsz[2], s))
+        if not learn:
+            return
+        self._launch_learn(stream)
+
+    def _launch_learn(self, stream):
+        L, P, s = dp.lib, dp._ptr, dp._stream(stream)
+        red, res = self.red, self.res
         rl = (ctypes.c_int * len(self.r_list))(*self.r_list)
         b1 = (ctypes.c_double * len(self.beta1))(*self.beta1)
         b2 = (ctypes.c_double * len(self.beta2))(*self.beta2)
@@ -106,7 +129,8 @@ class PipelineGraph:
     def capture(self, split=False):
         """Capture the pipeline into a CUDA graph (after one eager warm-up pass).  split: two
         graphs instead, graph_front (transform, Gram) and graph_back (reduce, learn), replayed by
-        replay_front / replay_back, so that a caller may place work between them."""
+        replay_front / replay_back, so that a caller may place work between them; split = 3:
+        graph_back is the reduce alone and graph_learn the learn step (replay_learn)."""
         side = torch.cuda.Stream(device=self.Q.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -118,7 +142,11 @@ class PipelineGraph:
             with torch.cuda.graph(self.graph_front):
                 self._launch(torch.cuda.current_stream(), back=False)
             with torch.cuda.graph(self.graph_back):
-                self._launch(torch.cuda.current_stream(), front=False)
+                self._launch(torch.cuda.current_stream(), front=False, learn=split != 3)
+            if split == 3:
+                self.graph_learn = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph_learn):
+                    self._launch_learn(torch.cuda.current_stream())
             return self
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
@@ -137,6 +165,9 @@ class PipelineGraph:
 
     def replay_back(self):
         self.graph_back.replay()
+
+    def replay_learn(self):
+        self.graph_learn.replay()
 
     def flags_value(self):
         """The OR of the DOPINF_FLAG_* bits raised so far (synchronises)."""
@@ -181,17 +212,97 @@ def upload(dst, src, chunks=8):
             dst[a:b].copy_(src[a:b], non_blocking=True)
 
 
+class OverlappedPipeline:
+    """Consecutive pipelines over two device-resident snapshot matrices (step i on copy i mod 2),
+    each step's front (transform, Gram: tensor cores and HBM) on a front stream beside the
+    previous step's learn step (rollouts: the FP64 pipe, most SMs idle in their tail) on the
+    compute stream.  The reduce steps stay in turn on the compute stream and no front runs beside
+    them (the tridiagonalisation is a cooperative launch whose CTAs must all be resident), and
+    the learn steps share one set of buffers, so they run one after the other.
+
+        front(i)  after reduce(i - 1)           (front stream)
+        reduce(i) after front(i) and learn(i-1) (compute stream)
+        learn(i)  after reduce(i)               (compute stream)
+
+    Every step computes its full pipeline; a step's results (res, red, flags of its copy) stay
+    valid until the next step's reduce starts."""
+
+    def __init__(self, Qs, var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, mode=dp.DISCRETE, dt=1.0,
+                 gram_mode=dp.GRAM_OZAKI_FP64, r_fixed=None, energy_target=0.9996, max_growth=1.2):
+        """Qs: two column-major (n x k) device matrices of the same shape, the snapshot matrix of
+        even and odd steps (each is transformed in place by its steps)."""
+        if len(Qs) != 2:
+            raise ValueError("Qs: two snapshot matrices")
+        kw = dict(mode=mode, dt=dt, gram_mode=gram_mode, r_fixed=r_fixed, energy_target=energy_target,
+                  max_growth=max_growth)
+        dev = Qs[0].device
+        self.pg = [PipelineGraph(Qs[0], var_row_offsets, r_cap, r_list, beta1, beta2, n_steps, **kw)]
+        self.pg.append(PipelineGraph(Qs[1], var_row_offsets, r_cap, r_list, beta1, beta2, n_steps,
+                                     share_back=self.pg[0], **kw))
+        for pg in self.pg:
+            pg.capture(split=3)
+        torch.cuda.synchronize(dev)
+        self.front_stream = torch.cuda.Stream(device=dev)
+        self.stream = torch.cuda.Stream(device=dev)
+        self.gram_done = [torch.cuda.Event() for _ in range(2)]
+        self.reduce_done = torch.cuda.Event()
+        self.reduce_done.record(torch.cuda.current_stream(dev))
+        self.count = 0
+
+    def submit(self, refill=None):
+        """Queue the next step; returns its index (its copy is index mod 2).  refill(Q): called
+        on the front stream before the step's transform, to enqueue writes of the step's input
+        into its copy Q (a device copy, an upload)."""
+        i, b = self.count, self.count % 2
+        pg = self.pg[b]
+        self.front_stream.wait_event(self.reduce_done)
+        with torch.cuda.stream(self.front_stream):
+            if refill is not None:
+                refill(pg.Q)
+            pg.replay_front()
+            self.gram_done[b].record(self.front_stream)
+        self.stream.wait_event(self.gram_done[b])
+        with torch.cuda.stream(self.stream):
+            pg.replay_back()
+            self.reduce_done.record(self.stream)
+            pg.replay_learn()
+        self.count += 1
+        return i
+
+    def join(self, stream=None):
+        """Make `stream` (default: the current stream) wait for everything submitted."""
+        st = stream if stream is not None else torch.cuda.current_stream()
+        st.wait_stream(self.front_stream)
+        st.wait_stream(self.stream)
+
+    def start_after(self, stream=None):
+        """Make the next submitted step wait for the work queued so far on `stream`."""
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.front_stream.wait_stream(st)
+        self.stream.wait_stream(st)
+
+    def results(self, i):
+        """Step i's outputs (device tensors; synchronises on the compute stream): valid for the
+        latest submitted step until another is submitted."""
+        if i != self.count - 1:
+            raise ValueError("only the latest step's results are held")
+        self.stream.synchronize()
+        pg = self.pg[i % 2]
+        return dict(res=pg.res, red=pg.red, flags=int(pg.flags.item()))
+
+
 class StreamingPipeline:
     """Steps II-IV over snapshot matrices that arrive one after another in pinned host memory.
 
     Two device copies of the snapshot matrix, each with its own captured front graph
-    (transform and Gram, the steps that read the matrix); reduce and learn form one shared back
-    graph (the workspaces and outputs are shared).  The upload of a matrix into a copy waits only
-    for the front graph that last read that copy (two steps back), so it runs on its copy stream
-    alongside the previous step (measured: such uploads do not slow the compute).  Each step's
-    results (training errors, statuses, the best index and its operators, the failure flags) are
-    copied back into pinned host memory on the compute stream; result(i) waits for step i's copy
-    and returns them.
+    (transform and Gram, the steps that read the matrix) and buffers; reduce and learn share
+    their workspaces and outputs.  Three streams, the schedule of OverlappedPipeline plus the
+    uploads: the upload of a matrix into a copy (copy stream) waits only for the front that last
+    read that copy (two steps back); a step's front (front stream) waits for its upload and for
+    the previous step's reduce, and so runs beside the previous step's learn step; reduce and
+    learn run in turn on the compute stream.  Each step's results (training errors, statuses,
+    the best index and its operators, the failure flags) are copied back into pinned host memory
+    on the compute stream; result(i) waits for step i's copy and returns them.
     """
 
     OUTS = ("train_err", "status", "best", "O_best")
@@ -213,17 +324,20 @@ class StreamingPipeline:
         self.pg = []
         for b in range(2):
             self.QT[b].copy_(host_QT)
-            share = self.pg[0] if b else None
+            share_back = self.pg[0] if b else None
             self.pg.append(PipelineGraph(self.QT[b].t(), var_row_offsets, r_cap, r_list, beta1, beta2, n_steps,
-                                         share=share, **kw).capture(split=True))
+                                         share_back=share_back, **kw).capture(split=3))
         torch.cuda.synchronize(dev)
         self.stream = torch.cuda.Stream(device=dev)
+        self.front_stream = torch.cuda.Stream(device=dev)
         self.copy_stream = torch.cuda.Stream(device=dev)
         self.front_done = [torch.cuda.Event() for _ in range(2)]  # the last front graph on QT[b] finished
         self.uploaded = [torch.cuda.Event() for _ in range(2)]    # QT[b] holds the next matrix
         self.fetched = [torch.cuda.Event() for _ in range(2)]     # host slot b holds a step's results
+        self.reduce_done = torch.cuda.Event()                     # the last reduce finished
         for e in self.front_done:
             e.record(torch.cuda.current_stream(dev))
+        self.reduce_done.record(torch.cuda.current_stream(dev))
         pg = self.pg[0]
         srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
         self.host_out = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in srcs] for _ in range(2)]
@@ -243,7 +357,7 @@ class StreamingPipeline:
         # the upload into copy b waits for the front graph that last read it (step i - 2)
         tm = None
         if self.times is not None:
-            tm = self.times[i] = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            tm = self.times[i] = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         self.copy_stream.wait_event(self.front_done[b])
         with torch.cuda.stream(self.copy_stream):
             if tm:
@@ -252,13 +366,20 @@ class StreamingPipeline:
             if tm:
                 tm[1].record(self.copy_stream)
             self.uploaded[b].record(self.copy_stream)
-        self.stream.wait_event(self.uploaded[b])
-        with torch.cuda.stream(self.stream):
+        self.front_stream.wait_event(self.uploaded[b])
+        self.front_stream.wait_event(self.reduce_done)
+        with torch.cuda.stream(self.front_stream):
             if tm:
-                tm[2].record(self.stream)
+                tm[2].record(self.front_stream)
             pg.replay_front()
-            self.front_done[b].record(self.stream)
-            self.pg[0].replay_back()
+            self.front_done[b].record(self.front_stream)
+        self.stream.wait_event(self.front_done[b])
+        with torch.cuda.stream(self.stream):
+            pg.replay_back()
+            self.reduce_done.record(self.stream)
+            if tm:
+                tm[4].record(self.stream)
+            pg.replay_learn()
             if tm:
                 tm[3].record(self.stream)
             srcs = [pg.res[name] for name in self.OUTS] + [pg.flags]
@@ -277,15 +398,18 @@ class StreamingPipeline:
         return self.uploaded[i % 2]
 
     def step_times(self, i):
-        """(upload ms, compute ms, gap ms) of step i (waits for it; record_times=True): the gap
-        is the time from the end of step i - 1's compute to the start of step i's, nonzero where
-        the compute waited for the upload (None for step 0)."""
+        """(upload ms, span ms, upload wait ms) of step i (waits for it; record_times=True): the
+        span runs from the start of the step's transform to the end of its learn step; the wait
+        is how long the step's upload ended after the previous step's reduce, i.e. how long the
+        front waited for its input (None for step 0)."""
         if self.times is None:
             raise ValueError("constructed without record_times")
         tm = self.times[i]
         tm[3].synchronize()
-        gap = self.times[i - 1][3].elapsed_time(tm[2]) if i - 1 in self.times else None
-        return tm[0].elapsed_time(tm[1]), tm[2].elapsed_time(tm[3]), gap
+        wait = None
+        if i - 1 in self.times:
+            wait = max(0.0, self.times[i - 1][4].elapsed_time(tm[1]))
+        return tm[0].elapsed_time(tm[1]), tm[2].elapsed_time(tm[3]), wait
 
     def result(self, i):
         """Step i's results on the host (waits for them); valid until step i + 2 is submitted."""

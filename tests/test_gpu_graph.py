@@ -55,6 +55,45 @@ def test_graph_replay_matches_synchronous_calls(dp, gram_mode):
         assert torch.equal(pg.res["O_best"], ref["O_best"])
 
 
+def test_overlapped_pipeline_matches_synchronous_calls(dp):
+    """Consecutive pipelines with the front of each step beside the previous step's learn step
+    (two streams, two snapshot copies) give every step the bits of the synchronous calls on its
+    own input."""
+    import dataclasses
+    from paper_2504_14338_gb300 import synth
+    from paper_2504_14338_gb300.graph import OverlappedPipeline
+    base = synth.WORKLOADS["small"]
+    r_list, r_cap, n_steps = [4, 6], 6, 300
+    b1 = synth.logspace(-8, 2, 3)
+    b2 = synth.logspace(-8, 2, 3)
+    inputs, refs = [], []
+    for seed in (11, 12):
+        w = dataclasses.replace(base, seed=seed)
+        Qn, _ = synth.snapshots_numpy(w)
+        Q0 = torch.from_numpy(np.asarray(Qn)).cuda()
+        Q = dp.snapshot_matrix(w.n, w.k)
+        Q.copy_(Q0)
+        dp.dopinf_transform(Q, w.var_row_offsets())
+        red = dp.dopinf_reduce(dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64), r_cap=r_cap, r_fixed=r_cap)
+        refs.append(dp.dopinf_learn(red["Qhat"], r_list, b1, b2, n_steps, mode=dp.CONTINUOUS_RK4, dt=w.snap_dt))
+        assert refs[-1]["best"] >= 0
+        inputs.append(Q0)
+    copies = [dp.snapshot_matrix(w.n, w.k) for _ in range(2)]
+    for c, q in zip(copies, inputs):
+        c.copy_(q)
+    op = OverlappedPipeline(copies, w.var_row_offsets(), r_cap, r_list, b1, b2, n_steps, mode=dp.CONTINUOUS_RK4,
+                            dt=w.snap_dt, gram_mode=dp.GRAM_OZAKI_FP64)
+    for i in range(5):  # inputs alternate with the copies; no synchronisation between steps
+        op.submit(refill=lambda Q, src=inputs[i % 2]: Q.copy_(src, non_blocking=True))
+        if i >= 3:
+            out = op.results(i)
+            ref = refs[i % 2]
+            assert out["flags"] == 0
+            assert int(out["res"]["best"].item()) == ref["best"]
+            for key in ("train_err", "growth", "status", "steps", "O_best"):
+                assert torch.equal(out["res"][key], ref[key]), (i, key)
+
+
 def test_batched_learn_graph_matches_each_problem(dp):
     """Several problems of uneven r (the batched-learn configuration at test scale: r drawn
     from a range, a 6 x 6 grid each) in one captured graph, each equal to its own learn call."""
@@ -83,8 +122,9 @@ def test_batched_learn_graph_matches_each_problem(dp):
 
 def test_streaming_pipeline_matches_synchronous_calls(dp):
     """Matrices streamed from pinned host memory through the double-buffered pipeline (uploads
-    overlapping the previous step): each step's host results equal the synchronous calls on
-    that matrix, and a result slot is only reused two steps later."""
+    and each step's transform and Gram overlapping the previous step): each step's host results
+    equal the synchronous calls on that matrix, and a result slot is only reused two steps
+    later."""
     import dataclasses
     from paper_2504_14338_gb300 import synth
     from paper_2504_14338_gb300.graph import StreamingPipeline
@@ -105,8 +145,11 @@ def test_streaming_pipeline_matches_synchronous_calls(dp):
         dp.dopinf_transform(Q, w.var_row_offsets())
         red = dp.dopinf_reduce(dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64), r_cap=r_cap, r_fixed=r_cap)
         refs.append(dp.dopinf_learn(red["Qhat"], r_list, b1, b2, n_steps, mode=mode, dt=dt))
-    sp = StreamingPipeline(mats[0], base.var_row_offsets(), r_cap, r_list, b1, b2, n_steps, mode=mode, dt=dt)
+    sp = StreamingPipeline(mats[0], base.var_row_offsets(), r_cap, r_list, b1, b2, n_steps, mode=mode, dt=dt,
+                           record_times=True)
     outs = sp.run(mats + mats[::-1])
+    up, span, wait = sp.step_times(5)
+    assert up > 0.0 and span > 0.0 and wait >= 0.0
     assert len(outs) == 6
     for out, ref in zip(outs, refs + refs[::-1]):
         assert out["flags"] == 0
