@@ -38,7 +38,7 @@ ROLLOUT_TRAFFIC = {"dw": None, "fp64": 12.03e6}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
@@ -738,6 +738,9 @@ def main():
         torch.cuda.synchronize()
         clk2 = Clocks()
         clk2.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         o0.record(stream)
         op.start_after(stream)
@@ -746,8 +749,14 @@ def main():
         op.join(stream)
         o1.record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         ck2 = clk2.stop()
         oms = o0.elapsed_time(o1) / args.steps
+        if world > 1:
+            tt = torch.tensor([oms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            oms = float(tt.item())
         last_out = op.results(op.count - 1)
         overlapped = {"ms_per_step": oms, "value": world / (oms / 1e3), "unit": UNIT, "steps": args.steps,
                       "flags": last_out["flags"], "best_index": int(last_out["res"]["best"].item()),
@@ -1012,6 +1021,14 @@ def main():
             batched = batched_learn_measure(dp, synth, dev, n_problems=args.batched_problems)
         except Exception as ex:
             batched = {"error": str(ex)}
+    # the headline: the overlapped schedule of consecutive pipelines (the library's
+    # OverlappedPipeline) where it ran cleanly; the serial step, stage by stage, beside it
+    serial = {"value": value, "ms_per_step": ms_per_step, "stages_ms": stage, "clocks": ck,
+              "how": "one pipeline after another on one stream (eager entry points), CUDA events around the steps"}
+    schedule = "serial"
+    if overlapped is not None and overlapped["flags"] == 0 and overlapped["best_index"] == res["best"]:
+        value, ms_per_step, ck = overlapped["value"], overlapped["ms_per_step"], overlapped["clocks"]
+        schedule = "overlapped"
     if rank == 0:
         best = res["best"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1027,6 +1044,7 @@ def main():
                                "rollouts": ("f32 double-word (~48 bits), statuses as in f64"
                                             if dp.dopinf_tune_rollout_arith(0) == dp.ROLLOUT_DW else "f64")},
                 "timing": "CUDA events on the launching stream around the timed steps; inputs larger than L2",
+                "schedule": schedule, "serial": serial,
                 "roofline": roof, "roofline_gram": roof_gram, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
                 "clocks": ck, "autotune": tuned, "graph_replay": graph, "overlapped": overlapped, "split_gram": split, "learn_vs_sequential": seq,
                 "learn_double_word_rollouts": dw_roll, "learn_qr_solver": qr, "step_v_lift": lift, "paper_shape": paper,
