@@ -10,7 +10,7 @@
 //     points shared by all eigenvalues over the whole GPU, then one CTA of 8 warps per
 //     eigenvalue, 256 trial points per round;
 //  3. their eigenvectors by inverse iteration with the partially pivoted tridiagonal LU,
-//     re-orthogonalised (modified Gram-Schmidt, twice) against earlier vectors whose
+//     re-orthogonalised (classical Gram-Schmidt, twice) against earlier vectors whose
 //     eigenvalues lie within 1e-3 ||T||;
 //  4. back-transformation by the stored reflectors in blocks of 16 (compact WY form), sign
 //     rule (largest-magnitude entry positive, lowest index on ties);
