@@ -463,6 +463,14 @@ def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16, group=128, seq
     ws = dp.Workspace(dev)
     dt = 0.01
     n_steps = 10_000
+    # the generators' trajectories (host work, seconds each) by a pool of spawned processes
+    wls = [synth.Workload("batched-%d" % p, 2, 4000, 1500, 40, seed=30_000 + p) for p in range(n_problems)]
+    if n_problems > 4:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+            trajs = pool.map(synth.trajectory, wls, chunksize=1)
+    else:
+        trajs = [synth.trajectory(w) for w in wls]
     n_seq = min(seq_problems, n_problems)
     seq_ids = sorted(set(int(i * n_problems // n_seq) for i in range(n_seq)))
     seq_set = []
@@ -472,8 +480,8 @@ def batched_learn_measure(dp, synth, dev, n_problems=8, n_sub=16, group=128, seq
         problems = []
         for p in range(g0, min(g0 + group, n_problems)):
             r = rs[p]
-            w = synth.Workload("batched-%d" % p, 2, 4000, 1500, 40, seed=30_000 + p)
-            Q = synth.snapshots_torch(w, dev).t()
+            w = wls[p]
+            Q = synth.snapshots_torch(w, dev, traj=trajs[p]).t()
             dp.dopinf_transform(Q, w.var_row_offsets(), ws=ws)
             D = dp.dopinf_gram(Q, mode=dp.GRAM_OZAKI_FP64, ws=ws)
             red = dp.dopinf_reduce(D, r_cap=r, r_fixed=r, ws=ws)

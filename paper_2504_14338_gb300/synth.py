@@ -175,15 +175,17 @@ def snapshots_numpy(w: Workload):
     return Q, dict(X=X, L=L, system=sysm)
 
 
-def snapshots_torch(w: Workload, device, col_major=True):
+def snapshots_torch(w: Workload, device, col_major=True, traj=None):
     """The same construction on a torch device, for workloads too large for the host.
 
     Returns Q as a torch tensor of shape (k, n) whose row t is snapshot t (i.e. the
     column-major n x k matrix with leading dimension n).  Draws come from torch's
     generator seeded with the workload seed, so values differ from snapshots_numpy.
+    traj: the trajectory of w as trajectory(w) returns it, when it was formed elsewhere
+    (it is the host-side part of the cost, a few seconds at r_true = 40, k = 1500).
     """
     import torch
-    X, _ = trajectory(w)
+    X, _ = trajectory(w) if traj is None else traj
     g = torch.Generator(device=device)
     g.manual_seed(w.seed)
     G = torch.randn(w.n, w.r_true, generator=g, device=device, dtype=torch.float64)
