@@ -60,3 +60,17 @@ def test_disjoint_cpu_list_changes_nothing(fake_topology, monkeypatch):
     (tmp / "local_cpulist").write_text("100-101\n")
     assert graph.bind_host_to_device("cuda:0") is None
     assert "set" not in calls
+
+
+def test_snapshots_torch_with_a_precomputed_trajectory():
+    """The device-side generator gives the same matrix whether it integrates the generating
+    system itself or is handed that trajectory (formed by another process), on the CPU."""
+    import numpy as np
+    import torch
+    from paper_2504_14338_gb300 import synth
+    w = synth.Workload("traj", 2, 64, 40, 5, seed=17)
+    a = synth.snapshots_torch(w, "cpu")
+    traj = synth.trajectory(w)
+    b = synth.snapshots_torch(w, "cpu", traj=traj)
+    assert torch.equal(a, b)
+    assert np.array_equal(traj[0], synth.trajectory(w)[0])
